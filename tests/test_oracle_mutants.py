@@ -1,0 +1,88 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case compiles a copy of ``oracle/dqmc_oracle.c`` with one planted mistake
+(a dropped term, a wrong index, a wrong operator, a skipped digit, an ignored
+don't-care set) and checks that brute force (Section 2 definitions) or a worked
+example rejects it.  Everything runs on the CPU.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import bruteforce as bf
+from paper_2302_10083_gb300 import synth
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "oracle", "dqmc_oracle.c")
+
+MUTANTS = {
+    "reduce_drops_t": ("S[it] = (uint8_t)(S[it] & !z);", ""),
+    "merge_or": ("S[iu] | (S[is] & S[it])", "S[iu] | (S[is] | S[it])"),
+    "merge_wrong_operand": ("S[iu] | (S[is] & S[it])", "S[iu] | (S[is] & S[is])"),
+    "skip_last_digit": ("for (int i = 1; i <= n; ++i) {\n        const uint64_t dd = d;\n"
+                        "        #pragma omp parallel for schedule(static) reduction(+:reduces)",
+                        "for (int i = 1; i < n; ++i) {\n        const uint64_t dd = d;\n"
+                        "        #pragma omp parallel for schedule(static) reduction(+:reduces)"),
+    "ignore_dc": ("(dc ? tt_bit(dc, t) : 0)", "0"),
+    "load_bit_order": ("if ((t >> i) & 1) r += w;", "if ((t >> (n - 1 - i)) & 1) r += w;"),
+    "reduce_reads_wrong_cell": ("const uint8_t z = S[iu];", "const uint8_t z = S[it];"),
+}
+
+
+def build_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    src = src.replace(old, new, 1)
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(src)
+    subprocess.run(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", str(so), str(c)],
+                   check=True)
+    L = ctypes.CDLL(str(so))
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    L.oracle_sweep.argtypes = [ctypes.c_int, u8p, u8p, u8p, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_uint64)]
+    L.oracle_sweep.restype = None
+
+    def sweep(n, on, dc=None):
+        S = np.empty(3 ** n, dtype=np.uint8)
+        cnt = (ctypes.c_uint64 * 2)()
+        on = np.ascontiguousarray(on, dtype=np.uint8)
+        dcp = None if dc is None else np.ascontiguousarray(dc, dtype=np.uint8)
+        L.oracle_sweep(n, on.ctypes.data_as(u8p),
+                       None if dcp is None else dcp.ctypes.data_as(u8p),
+                       S.ctypes.data_as(u8p), 1, cnt)
+        return S != 0
+    return sweep
+
+
+def pins_pass(sweep):
+    """A subset of the pins: brute force with and without don't-cares, majority."""
+    for n in (3, 5, 6):
+        for seed in (1, 2):
+            on, dc = synth.random_function(n, seed, 0.6, 0.25)
+            for d in (None, dc):
+                want = bf.primes(n, bf.support_of(n, on, d))
+                if not np.array_equal(sweep(n, on, d), want):
+                    return False
+    on = bf.bitmap_from_bool(bf.symmetric_support(3, {2, 3}))
+    got = np.nonzero(sweep(3, on))[0].tolist()
+    return got == [14, 16, 22]
+
+
+def test_unmutated_copy_passes(tmp_path):
+    old = MUTANTS["ignore_dc"][0]
+    MUTANTS["_identity"] = (old, old)
+    try:
+        assert pins_pass(build_mutant(tmp_path, "_identity"))
+    finally:
+        del MUTANTS["_identity"]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    assert not pins_pass(build_mutant(tmp_path, name)), name
