@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the dense ternary prime-implicant sweep (DenseQMC, arXiv 2302.10083).
+
+Workload: one n = 24 function, ON ~ Bernoulli(0.85) (seed 1 + rank), no
+don't-cares: 3^24 = 2.82e11 cubes.  One step = the whole hot path on the
+device: every sweep pass (truth table -> Merge -> fused Merge/Reduce ->
+Reduce -> dense prime bitmap + count) and the compaction of the bitmap into the
+(mask, value) list, with the truth table already in HBM.  The state (37 GB)
+and bitmap (35 GB) are far larger than the 129 MB L2, so no L2 flush is done
+between steps.
+
+Prints one JSON line (rank 0).  With --gpus N under torchrun every rank sweeps
+its own function (replicas, weak scaling; the passes need no exchange).
+
+--impl reference times the CPU oracle (plain C, Algorithm 3, one byte per
+cube, OpenMP on the host cores) on a bounded sample of the same workload
+family: the same generator and density at n = 19 per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_MAIN = 24
+P_ON = 0.85
+REF_SAMPLE_N = 19       # --impl reference: one oracle sweep of this size per step
+CPU_BASELINE_N = 20     # cpu_baseline: one oracle sweep of this size
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sel = [p for (t, p) in self.samples if t0 <= t <= t1] or [p for (_, p) in self.samples[-5:]]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [float(p[1]) for p in sel if p[1].replace(".", "").isdigit()]
+        smax = [float(p[2]) for p in sel if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in sel for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(sel)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_10083_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """dram read+write bytes per launch from profiles/ncu_traffic.json, if it was
+    taken from the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel_key)
+    return None if ent is None else ent.get("bytes_per_launch_full")
+
+
+def cpu_baseline(n=CPU_BASELINE_N):
+    import oracle
+    from paper_2302_10083_gb300 import synth
+    on, _ = synth.random_function(n, 1, P_ON)
+    t0 = time.perf_counter()
+    oracle.sweep(n, on)
+    dt = time.perf_counter() - t0
+    return {"value": 3 ** n / dt, "unit": "cubes/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"one n={n} function of the same family (ON ~ Bernoulli({P_ON}), seed 1): full oracle "
+                      f"sweep (Algorithm 3, one byte per cube, OpenMP), {dt:.2f} s; cubes/s = 3^{n}/time"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2302_10083_gb300 import synth
+    n = REF_SAMPLE_N
+    on, _ = synth.random_function(n, 1, P_ON)
+    for _ in range(args.warmup):
+        oracle.sweep(n, on)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sweep(n, on)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = 3 ** n / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": "cubes/s (dense prime-implicant sweep)", "value": value,
+        "unit": "cubes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"single function n={N_MAIN}, ON ~ Bernoulli({P_ON}); each reference step sweeps "
+                               f"an n={n} function of the same family", "n": N_MAIN, "sample_n": n},
+        "cpu_baseline": {"value": value, "unit": "cubes/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"n={n} oracle sweep per step (Algorithm 3, byte per cube)"},
+        "e2e": {"value": value, "unit": "cubes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_10083_gb300 import dqmc, synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n = args.n
+    seed = 1 + rank
+    on, _ = synth.random_function(n, seed, P_ON)
+    L = dqmc.lib()
+    # expected primes + 5% headroom sizes the list buffer
+    from math import comb
+    exp_primes = sum(comb(n, w) * 2 ** (n - w) * P_ON ** (2 ** w) * (1 - P_ON ** (2 ** w)) ** (n - w)
+                     for w in range(n + 1))
+    cap = int(exp_primes * 1.05) + 1024
+    buf = dqmc.DeviceBuffers(n, device=f"cuda:{local}", with_dc=False, cap=cap)
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    npass = dqmc.dqmc_plan_passes(n)
+    plan = dqmc.dqmc_plan_json(n)
+    names = [f"pass{i}:{q['kind']}{'+reduce' if q['fuse_reduce'] else ''}{'+bitmap' if q['write_out'] else ''}"
+             f"(K={q['K']},B={q['B']},a={q['a']})" for i, q in enumerate(plan["passes"])]
+    names.append("compact(count+scan+emit)")
+
+    def step(events=None):
+        for p in range(npass):
+            st = L.dqmc_sweep_pass_dev(n, p, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), buf.count.data_ptr(),
+                                       buf.work.data_ptr(), buf.work_bytes, sh)
+            if st != 0:
+                raise dqmc.DqmcError(st, f"pass {p}")
+            if events is not None:
+                events[p].record(stream)
+        st = L.dqmc_compact_dev(n, buf.bitmap.data_ptr(), buf.pairs.data_ptr(), cap, buf.count.data_ptr(),
+                                buf.work.data_ptr(), buf.work_bytes, sh)
+        if st != 0:
+            raise dqmc.DqmcError(st, "compact")
+        if events is not None:
+            events[npass].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    count = int(buf.count.item())
+    if count > cap:
+        raise SystemExit(f"list overflow: {count} primes > cap {cap}")
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    start.record(stream)
+    for k in range(K):
+        step(evs[k])
+    torch.cuda.synchronize()
+    barrier()
+    t_wall1 = time.time()
+    total_ms = start.elapsed_time(evs[K - 1][npass])
+    per_pass = [0.0] * (npass + 1)
+    for k in range(K):
+        prev = start if k == 0 else evs[k - 1][npass]
+        for p in range(npass + 1):
+            per_pass[p] += prev.elapsed_time(evs[k][p]) if p == 0 else evs[k][p - 1].elapsed_time(evs[k][p])
+    per_pass = [x / K for x in per_pass]
+    ms = total_ms / K
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = None
+    if sampler:
+        time.sleep(0.3)
+        sampler.stop()
+        clocks = sampler.summary(t_wall0, t_wall1)
+
+    cubes = 3 ** n
+    value = world * cubes / (ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    # dominant kernel = the sweep pass with the largest share of the step
+    dom = max(range(npass), key=lambda p: per_pass[p])
+    dom_bytes = dqmc.dqmc_pass_bytes(n, dom, False)
+    achieved = dom_bytes / (per_pass[dom] / 1e3) / 1e9
+    A = (cubes + 7) // 8
+    b_roof = (1 << n) // 8 + 3 * A
+    result = {
+        "metric": "cubes/s (dense prime-implicant sweep, n=24 single function)",
+        "value": value, "unit": "cubes/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 bitwise", "data": "synthetic",
+        "config": {"workload": f"single function n={n}, ON ~ Bernoulli({P_ON}), seed 1+rank, no don't-cares; "
+                               f"step = full sweep + bitmap + count + (mask,value) list, inputs resident in HBM",
+                   "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state 37 GB and bitmap 35 GB >> 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(f"pass{dom}"),
+                     "algorithmic_bytes_per_launch": dom_bytes},
+        "path_roofline": {"b_roof_bytes": b_roof, "achieved_gbs": b_roof / (ms / 1e3) / 1e9,
+                          "frac_of_peak": b_roof / (ms / 1e3) / 1e9 / peak,
+                          "note": "B_roof = 2^n/8 + 3*ceil(3^n/8): read input, write merged state, read it, write primes"},
+        "per_kernel_ms": {names[p]: per_pass[p] for p in range(npass + 1)},
+        "gpu_launches": K * (npass + 3),
+        "clocks": clocks,
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier, dist)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier, dist):
+    """Same metric through the host entry point dqmc_list: truth table from
+    pinned host memory in, (mask, value) list and count out to pinned host
+    memory, all inside the timed region."""
+    import ctypes
+
+    import numpy as np
+    del buf
+    torch.cuda.empty_cache()
+    L = dqmc.lib()
+    on_h = torch.from_numpy(np.ascontiguousarray(on)).pin_memory()
+    out_h = torch.empty(2 * cap, dtype=torch.int32).pin_memory()
+    cnt = ctypes.c_uint64()
+    on_p = ctypes.cast(on_h.data_ptr(), dqmc.c_u8p)
+    out_p = ctypes.cast(out_h.data_ptr(), dqmc.c_u32p)
+    steps = max(1, min(K, 5))
+    st = L.dqmc_list(n, on_p, None, out_p, cap, ctypes.byref(cnt))  # warm-up: device buffers allocated here
+    if st != 0:
+        raise dqmc.DqmcError(st, "dqmc_list")
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = L.dqmc_list(n, on_p, None, out_p, cap, ctypes.byref(cnt))
+        if st != 0:
+            raise dqmc.DqmcError(st, "dqmc_list")
+    dt = (time.perf_counter() - t0) / steps
+    if world > 1:
+        t = torch.tensor([dt], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    dqmc.dqmc_release()
+    return {"value": world * 3 ** n / dt, "unit": "cubes/s", "ms_per_step": 1e3 * dt, "steps": steps,
+            "h2d_bytes_per_step": int(on.size), "d2h_bytes_per_step": int(8 * cnt.value + 8),
+            "api": "dqmc_list (host buffers, pinned)"}
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,144 @@
+/*
+ * dqmc.h -- C ABI of libdqmc.so, the GB300 (sm_103a) dense ternary
+ * prime-implicant sweep of DenseQMC (arXiv 2302.10083).
+ *
+ * Problem (Section 1, "The Quine-McCluskey method", step 1; Section 2,
+ * Definitions of implicant and prime): given the truth table of
+ * f : {0,1}^n -> {0,1}, find every prime implicant of f.  Don't-cares are an
+ * extension: implicants are taken over the support I = ON u DC, and a prime
+ * whose minterms are all don't-cares is kept.
+ *
+ * Conventions (bind every entry point):
+ *  - Variable x_i (i = 1..n) is ternary digit i with weight 3^(i-1); a cube
+ *    s in {0,1,*}^n has index rho(s) = sum_i 3^(i-1) rho(s_i) with rho(0)=0,
+ *    rho(1)=1, rho(*)=2 (Section 4.2, the notation rho).
+ *  - Truth tables: ceil(2^n / 8) bytes, LSB first; minterm t = sum_i 2^(i-1) x_i
+ *    is bit t & 7 of byte t >> 3.  Bits t >= 2^n of the last byte are ignored.
+ *  - Prime bitmap: dense, unpadded, LSB first; bit rho(s) (byte rho >> 3, bit
+ *    rho & 7) is 1 iff s is a prime implicant.  dqmc_bitmap_bytes(n) =
+ *    ceil(3^n / 8) bytes; bits >= 3^n of the last byte are 0.
+ *  - List: pairs of uint32 (mask, value) in ascending rho: mask bit i-1 is 1
+ *    iff s_i is 0 or 1, value bit i-1 = s_i for those digits, else 0.  Cube s
+ *    covers minterm t iff (t & mask) == value.  out_pairs[2k] = mask,
+ *    out_pairs[2k+1] = value.
+ *  - 0 <= n <= DQMC_MAX_N.  n = 0 has one cube (the empty product), prime iff
+ *    f = 1.
+ *
+ * Errors: every call returns DQMC_OK (0) or a negative status and never
+ * aborts.  DQMC_EINVAL for a bad argument (n > DQMC_MAX_N, NULL on_bits, a
+ * workspace that is too small or misaligned), DQMC_ENOMEM when device memory
+ * cannot be had, DQMC_ETRUNC when a list does not fit in `cap` pairs (the
+ * first cap pairs and the true count are still written), DQMC_ECUDA for a CUDA
+ * runtime error (the call clears it; the context stays usable), DQMC_ETIMEOUT
+ * when a bounded device wait gave up.
+ *
+ * Ownership: the caller owns every buffer it passes.  Host entry points copy
+ * inputs to the device and results back; the device memory they use comes from
+ * a per-device cache owned by the library (released by dqmc_release()).  The
+ * *_dev entry points allocate nothing: the caller passes a device workspace of
+ * at least dqmc_workspace_bytes(n) bytes and every device pointer.
+ *
+ * Thread safety: host entry points serialise on a per-device lock; *_dev
+ * entry points only enqueue work on the given stream and may be called
+ * concurrently with different workspaces.
+ */
+#ifndef DQMC_H
+#define DQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    DQMC_OK = 0,
+    DQMC_EINVAL = -1,
+    DQMC_ENOMEM = -2,
+    DQMC_ETRUNC = -3,
+    DQMC_ECUDA = -4,
+    DQMC_ETIMEOUT = -5
+};
+
+/* Largest n handled: the padded state (3^(n-5) x 32 bytes) plus the bitmap of
+ * n = 25 take 218 GB, which fits the 288 GB of one GB300. */
+#define DQMC_MAX_N 25
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char *dqmc_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int dqmc_version(void);
+
+/* ceil(3^n / 8): bytes of the prime bitmap of an n-variable function
+ * (0 for n > DQMC_MAX_N). */
+uint64_t dqmc_bitmap_bytes(uint32_t n);
+
+/* Bytes a device bitmap buffer must have for the *_dev calls: the bitmap
+ * rounded up to a multiple of 16; the padding is written as zeros. */
+uint64_t dqmc_bitmap_alloc_bytes(uint32_t n);
+
+/* Device workspace needed by dqmc_primes_dev / dqmc_list_dev for this n
+ * (0 for n > DQMC_MAX_N).  It holds the padded ternary state (3^(n-5) rows of
+ * 32 bytes for n >= 13) and the list scan counters. */
+uint64_t dqmc_workspace_bytes(uint32_t n);
+
+/* ------------------------------------------------------------------ host API
+ * Host buffers in and out; synchronous.  dc_bits may be NULL (no don't-cares). */
+
+/* Prime bitmap of f (Algorithm 3 of Section 4.1 computed on the device; the
+ * result is the set of Section 2's prime implicants).  out_prime_bitmap:
+ * caller-owned, dqmc_bitmap_bytes(n) bytes; NULL computes and discards it. */
+int dqmc_primes(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+                uint8_t *out_prime_bitmap);
+
+/* Number of prime implicants (the popcount of the bitmap). */
+int dqmc_count(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+               uint64_t *out_count);
+
+/* The primes as (mask, value) pairs in ascending rho (the output extraction
+ * step of Algorithm 4, Section 4.2).  out_pairs: caller-owned, 2*cap uint32.
+ * *out_count receives the number of primes even when it exceeds cap
+ * (status DQMC_ETRUNC, first cap pairs written). */
+int dqmc_list(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+              uint32_t *out_pairs, uint64_t cap, uint64_t *out_count);
+
+/* Free the device memory cached by the host API on the current device. */
+void dqmc_release(void);
+
+/* ---------------------------------------------------------------- device API
+ * All pointers are device pointers (cudaMalloc / torch data_ptr), 16-byte
+ * aligned.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ * default stream) and the call returns without waiting.  d_work must be at
+ * least dqmc_workspace_bytes(n) bytes, 256-byte aligned, and must not be used
+ * by another call that overlaps on the device.  Inputs are read-only. */
+
+/* d_on, d_dc: ceil(2^n/8)-byte truth tables (d_dc may be NULL).
+ * d_bitmap: dqmc_bitmap_alloc_bytes(n) bytes, receives the prime bitmap.
+ * d_count: one uint64, receives the number of primes (may be NULL). */
+int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc,
+                    void *d_bitmap, uint64_t *d_count,
+                    void *d_work, uint64_t work_bytes, void *stream);
+
+/* Same sweep, then compaction of the bitmap into (mask, value) pairs.
+ * d_pairs: 2*cap uint32 (may be NULL when cap = 0).  d_count: one uint64,
+ * receives the number of primes (required).  Pairs at index >= cap are not
+ * written; the caller compares *d_count with cap after the stream completes. */
+int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc,
+                  void *d_bitmap, uint32_t *d_pairs, uint64_t cap,
+                  uint64_t *d_count, void *d_work, uint64_t work_bytes,
+                  void *stream);
+
+/* Compaction alone: (mask, value) pairs of the set bits of an existing dense
+ * bitmap of an n-variable function.  d_work as above (only its scan part is
+ * used).  d_count: one uint64 (required). */
+int dqmc_compact_dev(uint32_t n, const void *d_bitmap, uint32_t *d_pairs,
+                     uint64_t cap, uint64_t *d_count, void *d_work,
+                     uint64_t work_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQMC_H */

@@ -1,0 +1,53 @@
+/*
+ * dqmc_plan.h -- introspection of the pass plan libdqmc.so runs for a given n.
+ *
+ * The plan is the device schedule of Algorithm 3 (arXiv 2302.10083, Section
+ * 4.1): MergeAll over every digit, then ReduceAll over every digit.  Merge
+ * order and Reduce order are both free (the triples of one digit are
+ * independent, and Section 6 notes that the Reduce layers can be swapped), so
+ * the library merges the high digits in groups from the lowest up and
+ * reduces them in groups; this call reports which groups, in which passes.
+ * Host-only: it launches nothing and needs no GPU.
+ */
+#ifndef DQMC_PLAN_H
+#define DQMC_PLAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Writes a NUL-terminated JSON description of the plan for n variables into
+ * buf (at most cap bytes, truncated if needed) and returns the full length of
+ * the JSON text, or DQMC_EINVAL (-1) for n > DQMC_MAX_N.  buf may be NULL when
+ * cap is 0 (to query the length).  Fields: n, C (chunk digits, min(n, 5)),
+ * H (high digits), state_rows (32-byte rows of device state; 0 when the whole
+ * function fits one tile) and passes[] with kind ("first" | "merge" |
+ * "reduce"), K (group digits a .. a+K-1 among the high digits), B (inner
+ * digits 0 .. B-1 carried for contiguous rows), top_binary, fuse_reduce,
+ * chunk_reduce, write_out, tiles, n_mid, w_g, w_top. */
+int dqmc_plan_json(uint32_t n, char *buf, uint64_t cap);
+
+/* Number of passes (kernel launches of the sweep) for n variables, or
+ * DQMC_EINVAL for n > DQMC_MAX_N. */
+int dqmc_plan_passes(uint32_t n);
+
+/* Bytes pass `pass` must move by its design: 32 bytes per state row it reads
+ * and per state row it writes, plus the truth tables it reads and the bitmap
+ * bytes it writes.  0 for a bad n or pass. */
+uint64_t dqmc_pass_bytes(uint32_t n, int pass, int with_dc);
+
+/* Enqueue pass `pass` alone (same arguments as dqmc_primes_dev).  Running
+ * passes 0 .. dqmc_plan_passes(n)-1 in order on one stream is exactly
+ * dqmc_primes_dev; pass 0 also zeroes *d_count (or the workspace counter).
+ * Lets a caller put CUDA events between the kernels of the sweep. */
+int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const void *d_dc,
+                        void *d_bitmap, uint64_t *d_count, void *d_work,
+                        uint64_t work_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQMC_PLAN_H */

@@ -1,0 +1,237 @@
+"""ctypes binding of libdqmc.so (C ABI in include/dqmc.h and include/dqmc_plan.h).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  The functions named ``dqmc_*`` mirror the C entry points one to one;
+the short helpers below them (``primes``, ``count``, ``pairs``, ``*_tensor``)
+just allocate outputs for convenience.  There is no CPU fallback: if the
+library is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DQMC_OK = 0
+DQMC_EINVAL = -1
+DQMC_ENOMEM = -2
+DQMC_ETRUNC = -3
+DQMC_ECUDA = -4
+DQMC_ETIMEOUT = -5
+DQMC_MAX_N = 25
+
+_lock = threading.Lock()
+_lib = None
+
+c_u8p = ctypes.POINTER(ctypes.c_uint8)
+c_u32p = ctypes.POINTER(ctypes.c_uint32)
+c_u64p = ctypes.POINTER(ctypes.c_uint64)
+c_vp = ctypes.c_void_p
+
+
+class DqmcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})" if what else strerror(status))
+
+
+_SIGS = {
+    "dqmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "dqmc_version": (ctypes.c_int, []),
+    "dqmc_bitmap_bytes": (ctypes.c_uint64, [ctypes.c_uint32]),
+    "dqmc_bitmap_alloc_bytes": (ctypes.c_uint64, [ctypes.c_uint32]),
+    "dqmc_workspace_bytes": (ctypes.c_uint64, [ctypes.c_uint32]),
+    "dqmc_primes": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u8p]),
+    "dqmc_count": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u64p]),
+    "dqmc_list": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u32p, ctypes.c_uint64, c_u64p]),
+    "dqmc_release": (None, []),
+    "dqmc_primes_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
+    "dqmc_list_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp,
+                                     ctypes.c_uint64, c_vp]),
+    "dqmc_compact_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp,
+                                        ctypes.c_uint64, c_vp]),
+    "dqmc_plan_json": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_char_p, ctypes.c_uint64]),
+    "dqmc_plan_passes": (ctypes.c_int, [ctypes.c_uint32]),
+    "dqmc_pass_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int, ctypes.c_int]),
+    "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                           ctypes.c_uint64, c_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libdqmc.so (building it with nvcc first if needed and allowed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdqmc.so not found at {path}; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().dqmc_strerror(status).decode()
+
+
+def _check(status: int, what: str, ok=(DQMC_OK,)):
+    if status not in ok:
+        raise DqmcError(status, what)
+    return status
+
+
+def _host_tt(buf, n):
+    if buf is None:
+        return None
+    a = np.ascontiguousarray(np.frombuffer(bytes(buf), dtype=np.uint8) if not isinstance(buf, np.ndarray)
+                             else buf.view(np.uint8).reshape(-1))
+    if a.size < ((1 << n) + 7) >> 3:
+        raise ValueError("truth table too short")
+    return a
+
+
+def _p8(a):
+    return None if a is None else a.ctypes.data_as(c_u8p)
+
+
+# --------------------------------------------------------------- sizes, plan
+
+def dqmc_bitmap_bytes(n: int) -> int:
+    return int(lib().dqmc_bitmap_bytes(n))
+
+
+def dqmc_bitmap_alloc_bytes(n: int) -> int:
+    return int(lib().dqmc_bitmap_alloc_bytes(n))
+
+
+def dqmc_workspace_bytes(n: int) -> int:
+    return int(lib().dqmc_workspace_bytes(n))
+
+
+def dqmc_plan_json(n: int) -> dict:
+    L = lib()
+    need = L.dqmc_plan_json(n, None, 0)
+    _check(min(need, 0), "dqmc_plan_json")
+    buf = ctypes.create_string_buffer(need + 1)
+    L.dqmc_plan_json(n, buf, need + 1)
+    return json.loads(buf.value.decode())
+
+
+def dqmc_plan_passes(n: int) -> int:
+    return _check(lib().dqmc_plan_passes(n), "dqmc_plan_passes", ok=tuple(range(0, 1000)))
+
+
+def dqmc_pass_bytes(n: int, pass_index: int, with_dc: bool = False) -> int:
+    return int(lib().dqmc_pass_bytes(n, pass_index, int(with_dc)))
+
+
+# ----------------------------------------------------------------- host API
+
+def dqmc_primes(n: int, on_bits, dc_bits=None) -> np.ndarray:
+    """Prime bitmap (uint8, dqmc_bitmap_bytes(n)) through the host entry point."""
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    out = np.empty(max(dqmc_bitmap_bytes(n), 1), dtype=np.uint8)
+    _check(lib().dqmc_primes(n, _p8(on), _p8(dc), _p8(out)), "dqmc_primes")
+    return out[: dqmc_bitmap_bytes(n)]
+
+
+def dqmc_count(n: int, on_bits, dc_bits=None) -> int:
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    c = ctypes.c_uint64()
+    _check(lib().dqmc_count(n, _p8(on), _p8(dc), ctypes.byref(c)), "dqmc_count")
+    return int(c.value)
+
+
+def dqmc_list(n: int, on_bits, dc_bits=None, cap: int | None = None):
+    """(pairs (count, 2) uint32, count).  With cap=None the list is sized by a count call."""
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    if cap is None:
+        cap = dqmc_count(n, on, dc)
+    out = np.empty(2 * max(cap, 1), dtype=np.uint32)
+    c = ctypes.c_uint64()
+    st = lib().dqmc_list(n, _p8(on), _p8(dc), out.ctypes.data_as(c_u32p), cap, ctypes.byref(c))
+    _check(st, "dqmc_list", ok=(DQMC_OK, DQMC_ETRUNC))
+    k = min(int(c.value), cap)
+    return out[: 2 * k].reshape(k, 2), int(c.value)
+
+
+def dqmc_release() -> None:
+    lib().dqmc_release()
+
+
+# --------------------------------------------------------------- device API
+# Arguments are raw device addresses (ints, e.g. torch.Tensor.data_ptr()) and a
+# cudaStream_t handle as int (torch.cuda.Stream.cuda_stream).
+
+def dqmc_primes_dev(n, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream) -> int:
+    return _check(lib().dqmc_primes_dev(n, d_on, d_dc or None, d_bitmap, d_count or None, d_work, work_bytes,
+                                        stream or None), "dqmc_primes_dev")
+
+
+def dqmc_sweep_pass_dev(n, pass_index, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream) -> int:
+    return _check(lib().dqmc_sweep_pass_dev(n, pass_index, d_on, d_dc or None, d_bitmap, d_count or None, d_work,
+                                            work_bytes, stream or None), "dqmc_sweep_pass_dev")
+
+
+def dqmc_list_dev(n, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:
+    return _check(lib().dqmc_list_dev(n, d_on, d_dc or None, d_bitmap, d_pairs or None, cap, d_count, d_work,
+                                      work_bytes, stream or None), "dqmc_list_dev")
+
+
+def dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:
+    return _check(lib().dqmc_compact_dev(n, d_bitmap, d_pairs or None, cap, d_count, d_work, work_bytes,
+                                         stream or None), "dqmc_compact_dev")
+
+
+# ------------------------------------------------------- torch conveniences
+
+class DeviceBuffers:
+    """Device tensors for one n: inputs, bitmap, count, workspace (torch-owned)."""
+
+    def __init__(self, n: int, device="cuda", with_dc: bool = False, cap: int = 0):
+        import torch
+        self.n = n
+        tt = max(((1 << n) + 7) >> 3, 1)
+        tt_alloc = (tt + 15) // 16 * 16
+        self.on = torch.zeros(tt_alloc, dtype=torch.uint8, device=device)
+        self.dc = torch.zeros(tt_alloc, dtype=torch.uint8, device=device) if with_dc else None
+        self.bitmap = torch.empty(dqmc_bitmap_alloc_bytes(n), dtype=torch.uint8, device=device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        wb = dqmc_workspace_bytes(n)
+        self.work = torch.empty(max(wb, 256), dtype=torch.uint8, device=device)
+        self.work_bytes = self.work.numel()
+        self.cap = cap
+        self.pairs = torch.empty(2 * max(cap, 1), dtype=torch.int32, device=device)
+
+    def primes(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return dqmc_primes_dev(self.n, self.on.data_ptr(), self.dc.data_ptr() if self.dc is not None else None,
+                               self.bitmap.data_ptr(), self.count.data_ptr(), self.work.data_ptr(),
+                               self.work_bytes, s.cuda_stream)
+
+    def list(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return dqmc_list_dev(self.n, self.on.data_ptr(), self.dc.data_ptr() if self.dc is not None else None,
+                             self.bitmap.data_ptr(), self.pairs.data_ptr() if self.cap else None, self.cap,
+                             self.count.data_ptr(), self.work.data_ptr(), self.work_bytes, s.cuda_stream)

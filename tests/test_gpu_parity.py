@@ -1,0 +1,215 @@
+"""GPU parity: libdqmc.so (through its C ABI) against the CPU oracle.
+
+Bit-exact on the prime bitmap, the count and the (mask, value) list.  Small
+and medium n are compared element by element; n = 24 (the full-size
+workload) is checked on sampled cells with the oracle's pointwise definition,
+on every sampled listed prime, and by the structural properties that hold at
+any size.
+"""
+import numpy as np
+import pytest
+
+import bruteforce as bf
+import oracle
+from paper_2302_10083_gb300 import dqmc, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dqmc.lib()
+    yield
+    dqmc.dqmc_release()
+
+
+def check_all(n, on, dc=None):
+    S = oracle.sweep(n, on, dc)
+    want_bm = oracle.bitmap(n, S)
+    want_pairs = oracle.pairs(n, S)
+    got_bm = dqmc.dqmc_primes(n, on, dc)
+    assert got_bm.shape == want_bm.shape
+    if not np.array_equal(got_bm, want_bm):
+        bad = np.nonzero(got_bm != want_bm)[0]
+        raise AssertionError(f"n={n}: bitmap differs at {bad.size} bytes, first {bad[:8]}")
+    assert dqmc.dqmc_count(n, on, dc) == len(want_pairs)
+    pairs, cnt = dqmc.dqmc_list(n, on, dc)
+    assert cnt == len(want_pairs)
+    assert np.array_equal(pairs, want_pairs)
+
+
+@pytest.mark.parametrize("n", list(range(0, 13)))
+def test_whole_function_tile(n):
+    """n <= 12: one CTA holds the whole state in shared memory."""
+    for seed in (1, 2, 3):
+        for p in (0.3, 0.5, 0.85):
+            on, dc = synth.random_function(n, seed, p, 0.1 if seed == 2 else 0.0)
+            check_all(n, on, dc)
+
+
+def test_n10_workload():
+    for seed in (1, 2, 3):
+        on, dc = synth.single_n10(seed)
+        check_all(10, on, dc)
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+def test_multipass(n):
+    """n >= 13: First / Merge / fused Merge+Reduce / Reduce / bitmap passes."""
+    for seed, (p, q) in zip((1, 2), ((0.8, 0.0), (0.6, 0.15))):
+        on, dc = synth.random_function(n, seed, p, q)
+        check_all(n, on, dc)
+
+
+@pytest.mark.parametrize("n", [18, 19])
+def test_multipass_larger(n):
+    on, dc = synth.random_function(n, 5, 0.9, 0.05)
+    check_all(n, on, dc)
+
+
+def test_n20_workload():
+    """n = 20, ON ~ Bernoulli(0.7), DC ~ Bernoulli(0.1): bit-exact against the byte oracle."""
+    on, dc = synth.single_n20(1)
+    check_all(20, on, dc)
+
+
+def test_every_function_n3_and_sampled_n4():
+    for n in (2, 3):
+        for f, sup in bf.all_functions(n):
+            on = bf.bitmap_from_bool(sup)
+            want = oracle.bitmap(n, oracle.sweep(n, on))
+            assert np.array_equal(dqmc.dqmc_primes(n, on), want), (n, f)
+    for f in range(0, 1 << 16, 97):
+        on = np.array([f & 0xFF, f >> 8], dtype=np.uint8)
+        want = oracle.bitmap(4, oracle.sweep(4, on))
+        assert np.array_equal(dqmc.dqmc_primes(4, on), want), f
+
+
+@pytest.mark.parametrize("n", [0, 5, 12, 13, 17])
+def test_constants(n):
+    ones = np.full(synth.tt_bytes(n), 0xFF, dtype=np.uint8)
+    zeros = np.zeros(synth.tt_bytes(n), dtype=np.uint8)
+    pairs, c = dqmc.dqmc_list(n, ones)
+    assert c == 1 and pairs.tolist() == [[0, 0]]
+    bm = dqmc.dqmc_primes(n, ones)
+    assert bf.bool_from_bitmap(bm, n).nonzero()[0].tolist() == [3 ** n - 1]
+    assert dqmc.dqmc_count(n, zeros) == 0
+
+
+@pytest.mark.parametrize("n,W", [(3, {2, 3}), (12, {1, 2, 6, 7, 8, 12}), (15, {7, 8, 9, 10, 11, 12, 13, 14, 15}),
+                                 (16, set(range(1, 17, 2)))])
+def test_symmetric(n, W):
+    on = bf.bitmap_from_bool(bf.symmetric_support(n, W))
+    assert dqmc.dqmc_count(n, on) == bf.symmetric_prime_count(n, W)
+    if n <= 15:
+        got = bf.bool_from_bitmap(dqmc.dqmc_primes(n, on), n)
+        assert np.array_equal(got, bf.symmetric_prime_cells(n, W))
+
+
+def test_list_truncation():
+    n = 11
+    on, _ = synth.random_function(n, 4, 0.6)
+    want = oracle.pairs(n, oracle.sweep(n, on))
+    cap = len(want) // 3
+    pairs, cnt = dqmc.dqmc_list(n, on, None, cap=cap)
+    assert cnt == len(want)
+    assert np.array_equal(pairs, want[:cap])
+    L = dqmc.lib()
+    import ctypes
+    out = np.empty(2 * cap, dtype=np.uint32)
+    c = ctypes.c_uint64()
+    st = L.dqmc_list(n, on.ctypes.data_as(dqmc.c_u8p), None, out.ctypes.data_as(dqmc.c_u32p), cap,
+                     ctypes.byref(c))
+    assert st == dqmc.DQMC_ETRUNC and c.value == len(want)
+
+
+def test_device_api_with_torch_stream():
+    """dqmc_primes_dev / dqmc_list_dev on torch tensors and a side stream."""
+    n = 16
+    on, dc = synth.random_function(n, 8, 0.8, 0.1)
+    S = oracle.sweep(n, on, dc)
+    want_bm = oracle.bitmap(n, S)
+    want_pairs = oracle.pairs(n, S)
+    buf = dqmc.DeviceBuffers(n, with_dc=True, cap=len(want_pairs) + 5)
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    buf.dc[: dc.size].copy_(torch.from_numpy(dc))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    buf.list(stream=s)
+    s.synchronize()
+    got_bm = buf.bitmap[: want_bm.size].cpu().numpy()
+    assert np.array_equal(got_bm, want_bm)
+    assert not buf.bitmap[want_bm.size:].cpu().numpy().any()
+    assert int(buf.count.item()) == len(want_pairs)
+    got_pairs = buf.pairs[: 2 * len(want_pairs)].cpu().numpy().view(np.uint32).reshape(-1, 2)
+    assert np.array_equal(got_pairs, want_pairs)
+
+
+def test_repeat_calls_identical():
+    """The same call twice (workspace reused, stale state present) gives the same result."""
+    n = 15
+    a, _ = synth.random_function(n, 1, 0.9)
+    b, _ = synth.random_function(n, 2, 0.4)
+    ra = dqmc.dqmc_primes(n, a)
+    rb = dqmc.dqmc_primes(n, b)
+    assert np.array_equal(dqmc.dqmc_primes(n, a), ra)
+    assert np.array_equal(dqmc.dqmc_primes(n, b), rb)
+
+
+# ------------------------------------------------------------ n = 24 sampled
+
+def _sample_bits(bitmap_dev, rhos):
+    idx = torch.from_numpy((rhos >> 3).astype(np.int64)).to(bitmap_dev.device)
+    bytes_ = bitmap_dev[idx].cpu().numpy()
+    return ((bytes_ >> (rhos & 7).astype(np.uint8)) & 1).astype(bool)
+
+
+def test_n24_workload_sampled():
+    """n = 24, ON ~ Bernoulli(0.85), seed 1, in the launch configuration the
+    benchmark times (device API, list included): every sampled listed prime is
+    prime by definition, sampled cells agree with the pointwise oracle, the list
+    is ascending and matches the bitmap, and the count is within 1% of its
+    expectation."""
+    n = 24
+    on, _ = synth.single_n24(1)
+    expected = bf.expected_primes(n, 0.85)
+    cap = int(expected * 1.05)
+    buf = dqmc.DeviceBuffers(n, with_dc=False, cap=cap)
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    buf.list()
+    torch.cuda.synchronize()
+    count = int(buf.count.item())
+    assert abs(count - expected) / expected < 0.01
+    assert count <= cap
+    rng = np.random.default_rng(24)
+    k = np.unique(rng.integers(0, count, size=20000))
+    pairs = buf.pairs.view(-1, 2)[torch.from_numpy(k).cuda()].cpu().numpy().view(np.uint32)
+    # rho of each listed cube from (mask, value)
+    rho = np.zeros(len(k), dtype=np.int64)
+    for i in range(n):
+        d = np.where(((pairs[:, 0] >> i) & 1) == 0, 2, (pairs[:, 1] >> i) & 1).astype(np.int64)
+        rho += d * 3 ** i
+    assert np.all(np.diff(rho) > 0)                       # ascending
+    assert np.all(_sample_bits(buf.bitmap, rho))          # in the bitmap
+    assert np.all(oracle.is_prime_many(n, on, None, rho))  # prime by definition
+    cells = rng.integers(0, 3 ** n, size=200000, dtype=np.int64)
+    got = _sample_bits(buf.bitmap, cells)
+    want = oracle.is_prime_many(n, on, None, cells)
+    assert np.array_equal(got, want)
+    # the sweep's own popcount (bitmap pass) equals the compaction's count
+    c2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    dqmc.dqmc_primes_dev(n, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), c2.data_ptr(),
+                         buf.work.data_ptr(), buf.work_bytes, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(c2.item()) == count
+    # padding bits are zero
+    bm = buf.bitmap
+    nb = dqmc.dqmc_bitmap_bytes(n)
+    tail_bits = 3 ** n - 8 * (nb - 1)
+    last = int(bm[nb - 1].item())
+    assert last >> tail_bits == 0
+    assert not bm[nb:].any().item()
