@@ -202,8 +202,13 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
             } else {
                 const uint8_t *on8 = reinterpret_cast<const uint8_t *>(p.on);
                 const uint8_t *dc8 = reinterpret_cast<const uint8_t *>(p.dc);
+                // 2^C <= 16 minterms: one byte, two for C = 4
                 x = on8[0];
-                if (dc8) x |= dc8[0];
+                if constexpr (C == 4) x |= (uint32_t)on8[1] << 8;
+                if (dc8) {
+                    x |= dc8[0];
+                    if constexpr (C == 4) x |= (uint32_t)dc8[1] << 8;
+                }
                 x &= (1u << (1 << C)) - 1u;
             }
             uint32_t v[kChunkWords];
