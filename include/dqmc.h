@@ -130,6 +130,13 @@ int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc,
                   uint64_t *d_count, void *d_work, uint64_t work_bytes,
                   void *stream);
 
+/* Synchronises `stream`, then reports how the last sweep that used d_work
+ * ended: DQMC_OK, or DQMC_ETIMEOUT when a bounded device wait of the sweep
+ * (a tile waiting for the tiles it depends on, or the list's look-back) gave
+ * up after one second and the outputs are not valid.  Device waits never
+ * spin unbounded. */
+int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *stream);
+
 /* Compaction alone: (mask, value) pairs of the set bits of an existing dense
  * bitmap of an n-variable function.  d_work as above (only its scan part is
  * used).  d_count: one uint64 (required). */

@@ -1,6 +1,7 @@
 // dqmc_api.cu -- the C ABI of libdqmc.so (declared in include/dqmc.h and
 // include/dqmc_plan.h): argument checks, the pass plan, the workspace layout,
 // and the host entry points with their per-device buffer cache.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -18,14 +19,91 @@ static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 uint64_t bitmap_words(int n) { return (pow3(n) + 31) / 32; }
 uint64_t bitmap_alloc_bytes(int n) { return align_up((pow3(n) + 7) / 8, 16); }
 
-// Pass plan for n variables.
-//   n <= 12: one tile holds the whole function in shared memory (one pass).
-//   n >= 13: the high digits are split into a first group of 7 (contiguous
-//   rows) and groups of at most 6 (each row carried with its inner neighbour
-//   digit for 96-byte runs).  Merge goes group by group from the low digits;
-//   the last Merge pass also Reduces its digits and the chunk digits; the other
-//   groups are then Reduced from the top down, the first group last, and that
-//   pass writes the bitmap.
+// ------------------------------------------------------------------- plans
+//
+// n <= 12: one tile holds the whole function in shared memory (one pass of
+// the tile_pass kernel in dqmc_sweep.cu).
+//
+// n >= 13 (H = n - 5 >= 8 high digits), persistent super-passes
+// (dqmc_super.cu):
+//   1 first   truth table -> Merge chunk digits and high digits 0..5; rows with
+//             the digits >= 6 still 0/1;
+//   2 merge   Merge digits 6..9 (only when H > 10), sparse rows in and out;
+//   3 A       Merge digits 10..H-1 and Reduce them together with the five chunk
+//             digits (H <= 10: digits 6..H-1).  When there are more than five
+//             such digits they are split in two groups GA < GB and the
+//             super-block (inner digits + GA + GB) runs three phases: Merge GA,
+//             Merge + Reduce GB, Reduce GA.  This pass writes the whole state.
+//   4 B       Reduce digits 6..9 (phase a) and 0..5 (phase b, which writes the
+//             dense bitmap, the count and the list) on super-blocks of digits
+//             0..9 (H <= 10: phase b only).
+// Every digit is merged once before any Reduce and reduced exactly once; the
+// chunk digits in pass A.
+
+static FixedDigits fixed_of(const std::vector<int> &digits, const std::vector<bool> &merged)
+{
+    FixedDigits f;
+    for (int d : digits) {
+        f.w3[f.n] = pow3(d);
+        f.w2[f.n] = 1ull << d;
+        f.r[f.n] = merged[d] ? 3 : 2;
+        f.j[f.n] = (uint8_t)d;
+        ++f.n;
+    }
+    return f;
+}
+
+static uint64_t radix_product(const FixedDigits &f)
+{
+    uint64_t t = 1;
+    for (int i = 0; i < f.n; ++i) t *= f.r[i];
+    return t;
+}
+
+// A phase over group digits a..a+K-1 with inner digits 0..B-1 inside a
+// super-block whose digit set is sb_digits; the other super-block digits are
+// fixed per tile.
+static PhaseDesc make_phase(int load, int a, int K, int B, const std::vector<int> &sb_digits,
+                            const std::vector<bool> &merged)
+{
+    PhaseDesc ph;
+    ph.load = load;
+    ph.a = a;
+    ph.K = K;
+    ph.B = B;
+    std::vector<int> fixed;
+    for (int d : sb_digits)
+        if (d >= B && !(d >= a && d < a + K)) fixed.push_back(d);
+    ph.fix = fixed_of(fixed, merged);
+    ph.tiles = (uint32_t)radix_product(ph.fix);
+    return ph;
+}
+
+static void finish_superpass(SuperPassDesc &sp, const std::vector<int> &sb_digits, int H,
+                             const std::vector<bool> &merged_before, uint32_t window)
+{
+    std::vector<int> outer;
+    for (int d = 0; d < H; ++d)
+        if (std::find(sb_digits.begin(), sb_digits.end(), d) == sb_digits.end()) outer.push_back(d);
+    sp.sb = fixed_of(outer, merged_before);
+    sp.n_sb = radix_product(sp.sb);
+    sp.window = window ? window : (uint32_t)std::min<uint64_t>(sp.n_sb, 0xffffffffu);
+}
+
+static std::vector<int> range_digits(int lo, int hi)
+{
+    std::vector<int> v;
+    for (int d = lo; d < hi; ++d) v.push_back(d);
+    return v;
+}
+
+static std::vector<int> concat(std::vector<int> a, const std::vector<int> &b)
+{
+    a.insert(a.end(), b.begin(), b.end());
+    std::sort(a.begin(), a.end());
+    return a;
+}
+
 Plan make_plan(int n)
 {
     Plan p;
@@ -37,8 +115,6 @@ Plan make_plan(int n)
         Pass ps;
         ps.kind = kPassFirst;
         ps.K = H;
-        ps.B = 0;
-        ps.a = 0;
         ps.tiles = 1;
         ps.fuse_reduce = ps.chunk_reduce = ps.write_out = true;
         p.passes.push_back(ps);
@@ -46,86 +122,146 @@ Plan make_plan(int n)
         return p;
     }
     p.state_rows = pow3(H);
-    std::vector<int> starts, sizes;
-    starts.push_back(0);
-    sizes.push_back(kMaxSmemGroup);
-    const int rest = H - kMaxSmemGroup;
-    const int ng = (rest + kMaxStreamGroup - 1) / kMaxStreamGroup;
-    int at = kMaxSmemGroup;
-    for (int i = 0; i < ng; ++i) {
-        const int k = rest / ng + (i < rest % ng ? 1 : 0);
-        starts.push_back(at);
-        sizes.push_back(k);
-        at += k;
+    std::vector<bool> merged(H, false);
+    int slot = 0;
+
+    {   // 1: first -- digits 0..5 from the truth table
+        SuperPassDesc sp;
+        sp.nph = 1;
+        const std::vector<int> sbd = range_digits(0, 6);
+        sp.ph[0] = make_phase(kLoadTT, 0, 6, 0, sbd, merged);
+        sp.ph[0].merge = 1;
+        finish_superpass(sp, sbd, H, merged, 0);
+        sp.slot = slot++;
+        p.sps.push_back(sp);
+        for (int d = 0; d < 6; ++d) merged[d] = true;
     }
-    const int G = (int)sizes.size();
-    {   // first group: truth table -> rows with digits >= 7 binary
-        Pass ps;
-        ps.kind = kPassFirst;
-        ps.K = sizes[0];
-        ps.top_binary = true;
-        ps.w_top = pow3(sizes[0]);
-        ps.tiles = 1ull << (H - sizes[0]);
-        p.passes.push_back(ps);
+    const int top0 = H > 10 ? 10 : 6;  // first digit of pass A
+    if (H > 10) {   // 2: merge -- digits 6..9
+        SuperPassDesc sp;
+        sp.nph = 1;
+        const std::vector<int> sbd = concat(range_digits(0, 2), range_digits(6, 10));
+        sp.ph[0] = make_phase(kLoadSparse, 6, 4, 2, sbd, merged);
+        sp.ph[0].merge = 1;
+        finish_superpass(sp, sbd, H, merged, 0);
+        sp.slot = slot++;
+        p.sps.push_back(sp);
+        for (int d = 6; d < 10; ++d) merged[d] = true;
     }
-    for (int i = 1; i < G; ++i) {
-        const bool last = (i == G - 1);
-        Pass ps;
-        ps.kind = kPassMerge;
-        ps.K = sizes[i];
-        ps.B = 1;
-        ps.a = starts[i];
-        ps.n_mid = pow3(starts[i] - 1);
-        ps.w_g = pow3(starts[i]);
-        ps.w_top = pow3(starts[i] + sizes[i]);
-        ps.top_binary = !last;
-        const int top = H - starts[i] - sizes[i];
-        ps.tiles = ps.n_mid * (last ? 1ull : (1ull << top));
-        ps.fuse_reduce = ps.chunk_reduce = last;
-        p.passes.push_back(ps);
+    {   // 3: A -- Merge and Reduce digits top0..H-1, Reduce the chunk digits
+        const int m = H - top0;
+        SuperPassDesc sp;
+        if (m <= 5) {
+            const int B = 6 - m;
+            const std::vector<int> sbd = concat(range_digits(0, B), range_digits(top0, H));
+            sp.nph = 1;
+            sp.ph[0] = make_phase(kLoadSparse, top0, m, B, sbd, merged);
+            sp.ph[0].merge = sp.ph[0].reduce = 1;
+            sp.ph[0].chunk_mask = 31;
+            finish_superpass(sp, sbd, H, merged, 0);
+        } else {
+            const int m1 = m / 2, m2 = m - m1;   // m1 <= m2 <= 5
+            const int Ba = 6 - m1, Bb = 6 - m2;
+            const std::vector<int> sbd = concat(range_digits(0, Ba), range_digits(top0, H));
+            std::vector<bool> mg = merged;
+            sp.nph = 3;
+            sp.ph[0] = make_phase(kLoadSparse, top0, m1, Ba, sbd, mg);       // Merge GA
+            sp.ph[0].merge = 1;
+            for (int d = top0; d < top0 + m1; ++d) mg[d] = true;
+            sp.ph[1] = make_phase(kLoadSparse, top0 + m1, m2, Bb, sbd, mg);  // Merge + Reduce GB
+            sp.ph[1].merge = sp.ph[1].reduce = 1;
+            sp.ph[1].chunk_mask = 31;
+            for (int d = top0 + m1; d < H; ++d) mg[d] = true;
+            sp.ph[2] = make_phase(kLoadFull, top0, m1, Ba, sbd, mg);         // Reduce GA
+            sp.ph[2].reduce = 1;
+            finish_superpass(sp, sbd, H, merged, 2);
+        }
+        sp.slot = slot++;
+        p.sps.push_back(sp);
+        for (int d = top0; d < H; ++d) merged[d] = true;
     }
-    for (int i = G - 2; i >= 1; --i) {
-        Pass ps;
-        ps.kind = kPassReduce;
-        ps.K = sizes[i];
-        ps.B = 1;
-        ps.a = starts[i];
-        ps.n_mid = pow3(starts[i] - 1);
-        ps.w_g = pow3(starts[i]);
-        ps.w_top = pow3(starts[i] + sizes[i]);
-        ps.tiles = ps.n_mid * pow3(H - starts[i] - sizes[i]);
-        p.passes.push_back(ps);
+    {   // 4: B -- Reduce digits 6..9 (when pass A did not) and 0..5, write the bitmap
+        SuperPassDesc sp;
+        if (top0 == 10) {
+            const std::vector<int> sbd = range_digits(0, 10);
+            sp.nph = 2;
+            sp.ph[0] = make_phase(kLoadFull, 6, 4, 2, sbd, merged);
+            sp.ph[0].reduce = 1;
+            sp.ph[1] = make_phase(kLoadFull, 0, 6, 0, sbd, merged);
+            sp.ph[1].reduce = 1;
+            sp.ph[1].out = 1;
+            finish_superpass(sp, sbd, H, merged, 6);
+        } else {
+            const std::vector<int> sbd = range_digits(0, 6);
+            sp.nph = 1;
+            sp.ph[0] = make_phase(kLoadFull, 0, 6, 0, sbd, merged);
+            sp.ph[0].reduce = 1;
+            sp.ph[0].out = 1;
+            finish_superpass(sp, sbd, H, merged, 0);
+        }
+        sp.slot = slot++;
+        p.sps.push_back(sp);
     }
-    {
-        Pass ps;
-        ps.kind = kPassReduce;
-        ps.K = sizes[0];
-        ps.B = 0;
-        ps.a = 0;
-        ps.w_top = pow3(sizes[0]);
-        ps.tiles = pow3(H - sizes[0]);
-        ps.write_out = true;
-        p.passes.push_back(ps);
+    uint64_t done = 1 + kCtrlTickets;
+    for (auto &sp : p.sps) {
+        sp.done_off = done;
+        done += sp.n_sb * sp.nph;
     }
+    p.n_done = done - (1 + kCtrlTickets);
+    p.out_tiles = pow3(H) / kTileRowsMax;
     return p;
+}
+
+CtrlLayout ctrl_layout(const Plan &p)
+{
+    CtrlLayout c;
+    const uint64_t u32 = 1 + kCtrlTickets + p.n_done;
+    c.status_u64 = (u32 * 4 + 7) / 8;
+    c.bytes = align_up((c.status_u64 + p.out_tiles) * 8, 256);
+    return c;
+}
+
+int plan_passes(const Plan &p) { return p.sps.empty() ? (int)p.passes.size() : (int)p.sps.size(); }
+
+static std::string fixed_json(const FixedDigits &f)
+{
+    std::string s = "[";
+    for (int i = 0; i < f.n; ++i) {
+        s += (i ? "," : "");
+        s += "[" + std::to_string((int)f.j[i]) + "," + std::to_string((int)f.r[i]) + "]";
+    }
+    return s + "]";
 }
 
 std::string describe_plan(const Plan &p)
 {
     std::string s = "{\"n\":" + std::to_string(p.n) + ",\"C\":" + std::to_string(p.C) +
                     ",\"H\":" + std::to_string(p.H) + ",\"state_rows\":" + std::to_string(p.state_rows) +
-                    ",\"passes\":[";
-    for (size_t i = 0; i < p.passes.size(); ++i) {
-        const Pass &q = p.passes[i];
-        static const char *kinds[] = {"first", "merge", "reduce"};
-        char buf[512];
+                    ",\"out_tiles\":" + std::to_string(p.out_tiles) + ",\"passes\":[";
+    if (p.sps.empty()) {
+        const Pass &q = p.passes[0];
+        char buf[256];
         snprintf(buf, sizeof buf,
-                 "%s{\"kind\":\"%s\",\"K\":%d,\"B\":%d,\"a\":%d,\"top_binary\":%d,\"fuse_reduce\":%d,"
-                 "\"chunk_reduce\":%d,\"write_out\":%d,\"tiles\":%llu,\"n_mid\":%llu,\"w_g\":%llu,\"w_top\":%llu}",
-                 i ? "," : "", kinds[q.kind], q.K, q.B, q.a, (int)q.top_binary, (int)q.fuse_reduce,
-                 (int)q.chunk_reduce, (int)q.write_out, (unsigned long long)q.tiles,
-                 (unsigned long long)q.n_mid, (unsigned long long)q.w_g, (unsigned long long)q.w_top);
+                 "{\"kind\":\"whole\",\"n_sb\":1,\"window\":1,\"sb\":[],\"phases\":[{\"load\":\"tt\",\"K\":%d,"
+                 "\"B\":0,\"a\":0,\"merge\":1,\"reduce\":1,\"chunk_mask\":%d,\"out\":1,\"tiles\":1,\"fix\":[]}]}",
+                 q.K, (1 << p.C) - 1);
         s += buf;
+    }
+    static const char *loads[] = {"tt", "sparse", "full"};
+    for (size_t i = 0; i < p.sps.size(); ++i) {
+        const SuperPassDesc &sp = p.sps[i];
+        s += std::string(i ? "," : "") + "{\"kind\":\"super\",\"n_sb\":" + std::to_string(sp.n_sb) +
+             ",\"window\":" + std::to_string(sp.window) + ",\"sb\":" + fixed_json(sp.sb) + ",\"phases\":[";
+        for (int k = 0; k < sp.nph; ++k) {
+            const PhaseDesc &q = sp.ph[k];
+            char buf[256];
+            snprintf(buf, sizeof buf,
+                     "%s{\"load\":\"%s\",\"K\":%d,\"B\":%d,\"a\":%d,\"merge\":%d,\"reduce\":%d,\"chunk_mask\":%d,"
+                     "\"out\":%d,\"tiles\":%u,\"fix\":",
+                     k ? "," : "", loads[q.load], q.K, q.B, q.a, q.merge, q.reduce, q.chunk_mask, q.out, q.tiles);
+            s += buf + fixed_json(q.fix) + "}";
+        }
+        s += "]}";
     }
     s += "]}";
     return s;
@@ -141,6 +277,9 @@ Workspace workspace_layout(int n)
     at = align_up(at + w.state_bytes, 256);
     w.count_off = at;
     at = align_up(at + 256, 256);
+    w.ctrl_off = at;
+    w.ctrl_bytes = p.sps.empty() ? 256 : ctrl_layout(p).bytes;
+    at = align_up(at + w.ctrl_bytes, 256);
     w.n_blocks = (bitmap_words(n) + kListWordsPerBlock - 1) / kListWordsPerBlock;
     w.blk_counts_off = at;
     at = align_up(at + 4 * w.n_blocks, 256);
@@ -262,13 +401,46 @@ extern "C" int dqmc_plan_json(uint32_t n, char *buf, uint64_t cap)
 extern "C" int dqmc_plan_passes(uint32_t n)
 {
     if (n > DQMC_MAX_N) return DQMC_EINVAL;
-    return (int)make_plan((int)n).passes.size();
+    return plan_passes(make_plan((int)n));
+}
+
+// HBM bytes a super-pass must move by design: its first phase's reads (from
+// the previous pass) and its last writes (rows of the state, or the bitmap);
+// rows handed from one phase to the next stay in L2 and are not counted.
+static uint64_t super_bytes(const Plan &p, int i, bool with_dc)
+{
+    const SuperPassDesc &sp = p.sps[i];
+    const PhaseDesc &p0 = sp.ph[0];
+    const uint64_t RE = pow3(p0.B), NB = 1ull << p0.K, RG = pow3(p0.K);
+    const uint64_t tiles0 = (uint64_t)p0.tiles * sp.n_sb;
+    uint64_t rd = 0, wr = 0;
+    if (p0.load == kLoadTT) rd = tiles0 * NB * 4 * (with_dc ? 2 : 1);
+    else if (p0.load == kLoadSparse) rd = tiles0 * NB * RE * kChunkBytes;
+    else rd = tiles0 * RG * RE * kChunkBytes;
+    const PhaseDesc &pl = sp.ph[sp.nph - 1];
+    if (pl.out) {
+        wr = (pow3(p.n) + 7) / 8;
+    } else if (sp.nph == 1 && p0.load == kLoadSparse && !p0.reduce) {
+        wr = tiles0 * (RG - NB) * RE * kChunkBytes;     // only the rows the Merge created
+    } else {
+        // every row of the pass's super-blocks
+        uint64_t rows = sp.n_sb;
+        const PhaseDesc &q = sp.ph[0];
+        uint64_t inner = pow3(q.K) * pow3(q.B);
+        for (int k = 0; k < q.fix.n; ++k) inner *= 3;   // all digits merged by the end
+        rows *= inner;
+        wr = rows * kChunkBytes;
+    }
+    return rd + wr;
 }
 
 extern "C" uint64_t dqmc_pass_bytes(uint32_t n, int pass, int with_dc)
 {
     if (n > DQMC_MAX_N) return 0;
-    return pass_bytes(make_plan((int)n), pass, with_dc != 0);
+    const Plan p = make_plan((int)n);
+    if (p.sps.empty()) return pass_bytes(p, pass, with_dc != 0);
+    if (pass < 0 || pass >= (int)p.sps.size()) return 0;
+    return super_bytes(p, pass, with_dc != 0);
 }
 
 static int check_dev_args(uint32_t n, const void *d_on, const void *d_dc, const void *d_work,
@@ -283,21 +455,26 @@ static int check_dev_args(uint32_t n, const void *d_on, const void *d_dc, const 
 }
 
 static int sweep_dev(uint32_t n, int first, int last, const void *d_on, const void *d_dc, void *d_bitmap,
-                     uint64_t *d_count, void *d_work, uint64_t work_bytes, void *stream)
+                     uint64_t *d_count, void *d_work, uint64_t work_bytes, void *stream,
+                     uint32_t *d_pairs = nullptr, uint64_t cap = 0)
 {
     int st = check_dev_args(n, d_on, d_dc, d_work, work_bytes);
     if (st) return st;
     if (!d_bitmap || !aligned(d_bitmap, 16)) return DQMC_EINVAL;
     if (d_count && !aligned(d_count, 8)) return DQMC_EINVAL;
     const Plan plan = make_plan((int)n);
-    if (last < 0) last = (int)plan.passes.size();
-    if (first < 0 || first >= last || last > (int)plan.passes.size()) return DQMC_EINVAL;
+    const int np = plan_passes(plan);
+    if (last < 0) last = np;
+    if (first < 0 || first >= last || last > np) return DQMC_EINVAL;
     const Workspace w = workspace_layout((int)n);
     char *base = static_cast<char *>(d_work);
     unsigned long long *cnt = d_count ? reinterpret_cast<unsigned long long *>(d_count)
                                       : reinterpret_cast<unsigned long long *>(base + w.count_off);
-    return map_cuda(launch_sweep(plan, d_on, d_dc, base + w.state_off, static_cast<uint32_t *>(d_bitmap),
-                                 cnt, static_cast<cudaStream_t>(stream), first, last));
+    if (plan.sps.empty())
+        return map_cuda(launch_sweep(plan, d_on, d_dc, base + w.state_off, static_cast<uint32_t *>(d_bitmap),
+                                     cnt, static_cast<cudaStream_t>(stream), first, last));
+    return map_cuda(launch_super(plan, d_on, d_dc, base + w.state_off, static_cast<uint32_t *>(d_bitmap), cnt,
+                                 d_pairs, cap, base + w.ctrl_off, static_cast<cudaStream_t>(stream), first, last));
 }
 
 extern "C" int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
@@ -333,10 +510,27 @@ extern "C" int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc, voi
                              uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work,
                              uint64_t work_bytes, void *stream)
 {
-    if (!d_count) return DQMC_EINVAL;
+    if (!d_count || (cap && !d_pairs) || (d_pairs && !aligned(d_pairs, 8))) return DQMC_EINVAL;
+    if (n <= DQMC_MAX_N && !make_plan((int)n).sps.empty())  // the bitmap pass also writes the list
+        return sweep_dev(n, 0, -1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream,
+                         cap ? d_pairs : nullptr, cap);
     int st = dqmc_primes_dev(n, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream);
     if (st) return st;
     return dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
+}
+
+extern "C" int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *stream)
+{
+    if (n > DQMC_MAX_N || !d_work || work_bytes < workspace_layout((int)n).total) return DQMC_EINVAL;
+    const Workspace w = workspace_layout((int)n);
+    uint32_t err = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (make_plan((int)n).sps.empty()) return map_cuda(e);  // the one-tile pass has no device waits
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&err, static_cast<const char *>(d_work) + w.ctrl_off, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return map_cuda(e);
+    return err == 0 ? DQMC_OK : (err == kErrTimeout ? DQMC_ETIMEOUT : DQMC_ECUDA);
 }
 
 // Host entry points: copy in, run, copy out, wait.
@@ -375,6 +569,7 @@ static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, 
         e = cudaMemcpyAsync(out_bitmap, c->buf[2], dqmc_bitmap_bytes(n), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return map_cuda(e);
+    if ((st = dqmc_dev_status(n, c->buf[3], c->cap[3], s))) return st;
     const uint64_t count = *c->h_count;
     if (out_count) *out_count = count;
     if (want_list && cap) {

@@ -35,12 +35,58 @@ struct Pass {
     uint64_t w_top = 1;     // row weight of the first digit above the group: 3^(a+K)
 };
 
+// ---------------------------------------------------------------- super-passes
+// A super-pass is one persistent kernel launch.  Its rows are split into
+// super-blocks (a set of high digits varies inside a block, the others are
+// fixed per block); each super-block goes through up to three phases, and each
+// phase covers the block with tiles of <= 729 rows (group digits a..a+K-1 and
+// inner digits 0..B-1 vary inside a tile).  A tile of phase p > 0 starts only
+// after every tile of phase p-1 of its super-block is done, so the block's rows
+// stay in L2 between phases.
+constexpr int kMaxPhases = 3;
+constexpr int kMaxFixed = 24;
+constexpr int kTileRowsMax = 729;   // 3^6 rows x 32 bytes = 23 KB of shared memory
+
+enum LoadKind : int { kLoadTT = 0, kLoadSparse = 1, kLoadFull = 2 };
+
+struct FixedDigits {
+    int n = 0;
+    uint64_t w3[kMaxFixed] = {};    // row weight 3^j of high digit j
+    uint64_t w2[kMaxFixed] = {};    // truth-table word weight 2^j (used by kLoadTT)
+    uint8_t r[kMaxFixed] = {};      // 2: the digit still takes only 0/1 (not merged yet); 3: any
+    uint8_t j[kMaxFixed] = {};      // which high digit (for the plan description)
+};
+
+struct PhaseDesc {
+    int load = kLoadFull;
+    int K = 0, B = 0, a = 0;        // group digits a..a+K-1, inner digits 0..B-1
+    int merge = 0;                  // Merge the group digits (kLoadTT: chunk digits first)
+    int reduce = 0;                 // Reduce the group digits
+    int chunk_mask = 0;             // chunk digits Reduced here (bit i = chunk digit i)
+    int out = 0;                    // write the dense bitmap (+ count, + list) instead of rows
+    uint32_t tiles = 1;             // tiles per super-block = product of fix.r
+    FixedDigits fix;                // super-block digits fixed per tile
+};
+
+struct SuperPassDesc {
+    int nph = 1;
+    PhaseDesc ph[kMaxPhases];
+    uint64_t n_sb = 1;              // super-blocks = product of sb.r
+    uint32_t window = 1;            // super-blocks per pipeline step
+    FixedDigits sb;                 // digits fixed per super-block
+    uint64_t done_off = 0;          // offset (in uint32) of this pass's phase counters
+    int slot = 0;                   // ticket counter index
+};
+
 struct Plan {
     int n = 0;
     int C = 0;              // chunk digits: min(n, 5)
     int H = 0;              // high digits: n - C
     uint64_t state_rows = 0;    // rows of the device state (0: the state lives in shared memory)
-    std::vector<Pass> passes;
+    std::vector<Pass> passes;           // n <= 12: the one whole-function pass
+    std::vector<SuperPassDesc> sps;     // n >= 13: persistent super-passes
+    uint64_t n_done = 0;                // phase counters (uint32) over all super-passes
+    uint64_t out_tiles = 0;             // tiles of the bitmap phase (look-back slots)
 };
 
 constexpr int kMaxSmemGroup = 7;    // 3^7 rows x 32 B = 70 KB of shared memory
@@ -53,6 +99,7 @@ std::string describe_plan(const Plan &p);
 struct Workspace {
     uint64_t state_off = 0, state_bytes = 0;
     uint64_t count_off = 0;             // uint64 scratch counter
+    uint64_t ctrl_off = 0, ctrl_bytes = 0;  // error word, tickets, phase counters, look-back slots
     uint64_t blk_counts_off = 0;        // uint32 per compaction block
     uint64_t blk_offs_off = 0;          // uint64 per compaction block
     uint64_t n_blocks = 0;
@@ -72,6 +119,26 @@ cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc,
 
 // Bytes pass i moves by design (rows read and written x 32, truth tables, bitmap).
 uint64_t pass_bytes(const Plan &plan, int i, bool with_dc);
+
+// Control block at the start of ctrl_off: uint32 error word, then ticket
+// counters, then phase counters, then (8-aligned) uint64 look-back slots.
+constexpr int kCtrlTickets = 8;
+struct CtrlLayout {
+    uint64_t err = 0;           // uint32 index
+    uint64_t tickets = 1;       // uint32 index
+    uint64_t done = 1 + kCtrlTickets;
+    uint64_t status_u64 = 0;    // uint64 index from ctrl base
+    uint64_t bytes = 0;
+};
+CtrlLayout ctrl_layout(const Plan &p);
+
+// Status word written by a timed-out device wait (dqmc_dev_status reads it).
+constexpr uint32_t kErrTimeout = 0x54494d45u;  // "TIME"
+
+// Enqueue the super-passes of a plan (n >= 13).  d_pairs may be null (no list).
+cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
+                         uint32_t *d_bitmap, unsigned long long *d_count, uint32_t *d_pairs,
+                         uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last);
 
 // Enqueue compaction of a dense bitmap into (mask, value) pairs.
 constexpr int kListWordsPerBlock = 4096;

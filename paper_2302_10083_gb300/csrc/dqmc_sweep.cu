@@ -424,14 +424,8 @@ cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc, v
         a.fuse_reduce = ps.fuse_reduce;
         a.chunk_reduce = ps.chunk_reduce;
         a.write_out = ps.write_out;
-        switch (ps.kind) {
-        case kPassFirst: e = dispatch_k<kPassFirst, 0>(plan.C, ps, a, stream); break;
-        case kPassMerge: e = (ps.B == 1) ? dispatch_k<kPassMerge, 1>(plan.C, ps, a, stream)
-                                         : cudaErrorInvalidValue; break;
-        case kPassReduce: e = (ps.B == 1) ? dispatch_k<kPassReduce, 1>(plan.C, ps, a, stream)
-                                          : dispatch_k<kPassReduce, 0>(plan.C, ps, a, stream); break;
-        default: e = cudaErrorInvalidValue;
-        }
+        // n <= 12 only: one tile, the whole function (n >= 13 runs dqmc_super.cu)
+        e = (ps.kind == kPassFirst) ? dispatch_k<kPassFirst, 0>(plan.C, ps, a, stream) : cudaErrorInvalidValue;
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -57,6 +57,7 @@ _SIGS = {
                                         ctypes.c_uint64, c_vp]),
     "dqmc_plan_json": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_char_p, ctypes.c_uint64]),
     "dqmc_plan_passes": (ctypes.c_int, [ctypes.c_uint32]),
+    "dqmc_dev_status": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_pass_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int, ctypes.c_int]),
     "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp,
                                            ctypes.c_uint64, c_vp]),
@@ -197,6 +198,10 @@ def dqmc_list_dev(n, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_b
                                       work_bytes, stream or None), "dqmc_list_dev")
 
 
+def dqmc_dev_status(n, d_work, work_bytes, stream) -> int:
+    return _check(lib().dqmc_dev_status(n, d_work, work_bytes, stream or None), "dqmc_dev_status")
+
+
 def dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:
     return _check(lib().dqmc_compact_dev(n, d_bitmap, d_pairs or None, cap, d_count, d_work, work_bytes,
                                          stream or None), "dqmc_compact_dev")
@@ -228,6 +233,11 @@ class DeviceBuffers:
         return dqmc_primes_dev(self.n, self.on.data_ptr(), self.dc.data_ptr() if self.dc is not None else None,
                                self.bitmap.data_ptr(), self.count.data_ptr(), self.work.data_ptr(),
                                self.work_bytes, s.cuda_stream)
+
+    def status(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return dqmc_dev_status(self.n, self.work.data_ptr(), self.work_bytes, s.cuda_stream)
 
     def list(self, stream=None):
         import torch

@@ -76,32 +76,14 @@ def plan(n):
     return dqmc.dqmc_plan_json(n)
 
 
-@pytest.mark.parametrize("n", list(range(0, 26)))
-def test_plan_digit_coverage(n):
-    p = plan(n)
-    C, H = p["C"], p["H"]
-    assert C == min(n, 5) and H == n - C
-    merged, reduced, chunk_reduced = [], [], 0
-    for q in p["passes"]:
-        digits = list(range(q["a"], q["a"] + q["K"]))
-        if q["kind"] in ("first", "merge"):
-            merged += digits
-            if q["fuse_reduce"]:
-                reduced += digits
-        else:
-            reduced += digits
-        chunk_reduced += q["chunk_reduce"]
-        assert q["K"] + q["B"] <= 7
-    assert sorted(merged) == list(range(H))
-    assert sorted(reduced) == list(range(H))
-    assert chunk_reduced == 1
-    # merge groups ascend; the bitmap is written by the last pass only
-    assert [q["write_out"] for q in p["passes"]] == [False] * (len(p["passes"]) - 1) + [True]
-    assert p["passes"][0]["kind"] == "first"
-    if H > 7:
-        assert p["state_rows"] == 3 ** H
-        out = p["passes"][-1]
-        assert out["a"] == 0 and out["B"] == 0  # contiguous rows for the dense write
+def decode_fixed(fix, x):
+    """Mixed-radix decode exactly as the kernel: first entry least significant."""
+    row = 0
+    for digit, radix in fix:
+        d = x % radix
+        x //= radix
+        row += d * 3 ** digit
+    return row
 
 
 def spread3(x):
@@ -114,15 +96,10 @@ def spread3(x):
     return r
 
 
-def tile_rows(q, tile, binary_group):
-    """Rows a tile touches, with the same formulas as the kernel."""
-    RE, K = 3 ** q["B"], q["K"]
-    mid = tile % q["n_mid"]
-    topi = tile // q["n_mid"]
-    top_t = spread3(topi) if q["top_binary"] else topi
-    base = mid * RE + top_t * q["w_top"]
+def tile_rows(ph, base, binary_group):
+    RE, K = 3 ** ph["B"], ph["K"]
     gs = [spread3(b) for b in range(1 << K)] if binary_group else range(3 ** K)
-    return [base + e + g * q["w_g"] for g in gs for e in range(RE)]
+    return [base + e + g * 3 ** ph["a"] for g in gs for e in range(RE)]
 
 
 def row_digits(r, H):
@@ -133,42 +110,176 @@ def row_digits(r, H):
     return d
 
 
-@pytest.mark.parametrize("n", [13, 14, 16, 17])
+@pytest.mark.parametrize("n", list(range(0, 26)))
+def test_plan_digit_coverage(n):
+    p = plan(n)
+    C, H = p["C"], p["H"]
+    assert C == min(n, 5) and H == n - C
+    merged, reduced, chunk = [], [], 0
+    merge_done = False
+    for sp in p["passes"]:
+        for ph in sp["phases"]:
+            digits = list(range(ph["a"], ph["a"] + ph["K"]))
+            assert ph["K"] + ph["B"] <= (7 if sp["kind"] == "whole" else 6)
+            assert ph["B"] <= ph["a"] or ph["K"] == 0 or ph["a"] == 0
+            if ph["merge"]:
+                assert not merge_done or ph["reduce"], "a Merge after the first Reduce"
+                merged += digits
+            if ph["reduce"]:
+                # every digit is merged before the first Reduce
+                merge_done = True
+                reduced += digits
+            chunk += bin(ph["chunk_mask"]).count("1")
+    assert sorted(merged) == list(range(H))
+    assert sorted(reduced) == list(range(H))
+    assert chunk == C
+    last = p["passes"][-1]["phases"][-1]
+    assert last["out"] == 1
+    outs = [ph["out"] for sp in p["passes"] for ph in sp["phases"]]
+    assert sum(outs) == 1
+    if H > 7:
+        assert p["state_rows"] == 3 ** H
+        assert last["a"] == 0 and last["B"] == 0 and last["K"] == 6
+        assert p["out_tiles"] == 3 ** H // 729
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
 def test_plan_tiles_cover_rows(n):
-    """Every pass touches exactly the rows it must, each once."""
+    """Every phase's tiles touch exactly the rows they must, each once; sparse
+    loads read exactly the rows earlier phases wrote."""
     p = plan(n)
     H = p["H"]
-    done = set()            # digits merged so far
-    for q in p["passes"]:
-        grp = set(range(q["a"], q["a"] + q["K"]))
-        writes = []
-        reads = []
-        for t in range(q["tiles"]):
-            if q["kind"] == "first":
-                writes += tile_rows(q, t, False)
-            elif q["kind"] == "merge":
-                reads += tile_rows(q, t, True)
-                writes += tile_rows(q, t, False)
-            else:
-                reads += tile_rows(q, t, False)
-                writes += tile_rows(q, t, False)
-        assert len(set(writes)) == len(writes), "tiles overlap"
-        assert all(0 <= r < 3 ** H for r in writes)
-        if q["kind"] in ("first", "merge"):
-            after = done | grp
-            # written rows: merged digits any value, the rest binary
-            want = [r for r in range(3 ** H)
-                    if all(dg != 2 or j in after for j, dg in enumerate(row_digits(r, H)))]
-            assert sorted(writes) == want
-            if q["kind"] == "merge":
-                # read rows: group digits and unmerged digits binary, all previously written
-                want_r = [r for r in range(3 ** H)
-                          if all(dg != 2 or j in done for j, dg in enumerate(row_digits(r, H)))]
-                assert sorted(reads) == want_r
-            done = after
-        else:
-            assert sorted(writes) == list(range(3 ** H))
+    merged = set()
+    written = set()
+    for sp in p["passes"]:
+        sb_digits = sorted(set(range(H)) - {d for d, _ in sp["sb"]})
+        for ph in sp["phases"]:
+            grp = set(range(ph["a"], ph["a"] + ph["K"]))
+            reads, writes = [], []
+            for sb in range(sp["n_sb"]):
+                b0 = decode_fixed(sp["sb"], sb)
+                for t in range(ph["tiles"]):
+                    base = b0 + decode_fixed(ph["fix"], t)
+                    if ph["load"] == "sparse":
+                        reads += tile_rows(ph, base, True)
+                    elif ph["load"] == "full":
+                        reads += tile_rows(ph, base, False)
+                    writes += tile_rows(ph, base, False)
+            assert len(set(writes)) == len(writes), "tiles overlap"
+            assert all(0 <= r < 3 ** H for r in writes)
+            after = merged | (grp if ph["merge"] else set())
+            want = {r for r in range(3 ** H)
+                    if all(dg != 2 or j in after for j, dg in enumerate(row_digits(r, H)))}
+            assert set(writes) == want
+            if ph["load"] == "sparse":
+                got = set(reads)
+                assert got == {r for r in want if all(row_digits(r, H)[j] != 2 for j in grp)}
+                assert got <= written
+            elif ph["load"] == "full":
+                assert set(reads) == want and set(reads) <= written
+            written |= set(writes)
+            merged = after
+        # super-block digit set: group + inner + phase-fixed digits of every phase
+        for ph in sp["phases"]:
+            inside = set(range(ph["B"])) | set(range(ph["a"], ph["a"] + ph["K"])) | {d for d, _ in ph["fix"]}
+            assert inside == set(sb_digits) or sp["kind"] == "whole"
 
+
+@pytest.mark.parametrize("n", list(range(13, 26)))
+def test_plan_rows_in_bounds(n):
+    """Extreme tiles stay below 3^H; tile and ticket counts fit the kernel's types."""
+    p = plan(n)
+    H = p["H"]
+    for sp in p["passes"]:
+        last_sb = decode_fixed(sp["sb"], sp["n_sb"] - 1)
+        tickets = 0
+        for ph in sp["phases"]:
+            top = last_sb + decode_fixed(ph["fix"], ph["tiles"] - 1)
+            row_max = top + 3 ** ph["B"] - 1 + (3 ** ph["K"] - 1) * 3 ** ph["a"]
+            assert row_max < 3 ** H
+            assert 3 ** (ph["K"] + ph["B"]) <= 729
+            tickets += ph["tiles"] * sp["n_sb"]
+            if ph["load"] == "tt":
+                # truth-table words: binary value of the fixed digits times 2^K + gb < 2^H
+                tt = sum(2 ** d for d, r in sp["sb"]) + 2 ** ph["K"] - 1
+                assert tt < 2 ** H
+            if ph["out"]:
+                assert ph["a"] == 0 and ph["B"] == 0 and ph["K"] == 6
+        assert tickets < 2 ** 32
+
+
+# ------------------------------------------------- ticket order (host replica)
+
+def step_offset(sp, k):
+    off = 0
+    for p_, ph in enumerate(sp["phases"]):
+        if k <= p_:
+            continue
+        off += min((k - p_) * sp["window"], sp["n_sb"]) * ph["tiles"]
+    return off
+
+
+def decode_ticket(sp, ticket):
+    nph = len(sp["phases"])
+    groups = -(-sp["n_sb"] // sp["window"])
+    lo, hi = 0, groups + nph - 1
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if step_offset(sp, mid) <= ticket:
+            lo = mid
+        else:
+            hi = mid
+    rem = ticket - step_offset(sp, lo)
+    for p_, ph in enumerate(sp["phases"]):
+        if lo < p_:
+            break
+        g = lo - p_
+        if g >= groups:
+            continue
+        nsb = min(sp["window"], sp["n_sb"] - g * sp["window"])
+        cnt = nsb * ph["tiles"]
+        if rem < cnt:
+            return p_, g * sp["window"] + rem // ph["tiles"], rem % ph["tiles"]
+        rem -= cnt
+    raise AssertionError("ticket out of range")
+
+
+@pytest.mark.parametrize("n", [13, 15, 16, 18, 21, 24])
+def test_ticket_order_is_a_valid_schedule(n):
+    """The device's ticket -> (phase, super-block, tile) map is a bijection and
+    every tile's dependencies (all tiles of the previous phase of its block)
+    hold smaller tickets; bitmap tiles come in ascending rho order."""
+    p = plan(n)
+    for sp in p["passes"]:
+        if sp["kind"] == "whole":
+            continue
+        total = sum(ph["tiles"] for ph in sp["phases"]) * sp["n_sb"]
+        budget = 400000
+        if total > budget:
+            # large plans: same window, truncated to a few super-block groups
+            sp = dict(sp, n_sb=min(sp["n_sb"], 7 * sp["window"] + 3))
+            total = sum(ph["tiles"] for ph in sp["phases"]) * sp["n_sb"]
+        seen = {}
+        last_of = {}
+        for tk in range(total):
+            key = decode_ticket(sp, tk)
+            assert key not in seen
+            seen[key] = tk
+            last_of[(key[0], key[1])] = max(last_of.get((key[0], key[1]), -1), tk)
+        assert len(seen) == total
+        for (ph, sb, t), tk in seen.items():
+            if ph > 0:
+                assert last_of[(ph - 1, sb)] < tk
+        out_phase = [i for i, ph in enumerate(sp["phases"]) if ph["out"]]
+        if out_phase:
+            op = out_phase[0]
+            bases = sorted((tk, decode_fixed(sp["sb"], sb) + decode_fixed(sp["phases"][op]["fix"], t))
+                           for (ph, sb, t), tk in seen.items() if ph == op)
+            rows = [b for _, b in bases]
+            assert rows == sorted(rows)
+
+
+# ------------------------------------------------- semantic simulation
 
 def grouped_reduce(S, n, digits):
     """Reduce over a set of digits, every read taken from the state as it was before."""
@@ -195,10 +306,10 @@ def merge_digit(S, n, j):
     return A.reshape(-1)
 
 
-@pytest.mark.parametrize("n,seed", [(8, 1), (13, 2), (14, 3), (15, 4)])
+@pytest.mark.parametrize("n,seed", [(8, 1), (13, 2), (14, 3), (15, 4), (16, 5)])
 def test_plan_schedule_simulated(n, seed):
-    """Run the plan's digit schedule on the host (Merge per digit, Reduce grouped
-    per pass from the pass's starting state) and compare with the oracle."""
+    """Run the plan's digit schedule on the host (Merge digit by digit, Reduce
+    grouped per phase from the phase's starting state) against the oracle."""
     on, dc = synth.random_function(n, seed, 0.75, 0.1)
     p = plan(n)
     C = p["C"]
@@ -210,41 +321,17 @@ def test_plan_schedule_simulated(n, seed):
     for i in range(n):
         rho += ((t >> i) & 1) * 3 ** i
     S[rho] = sup
-    chunk_digits = list(range(C))
-    for q in p["passes"]:
-        grp = [C + d for d in range(q["a"], q["a"] + q["K"])]
-        if q["kind"] in ("first", "merge"):
-            digits = (chunk_digits if q["kind"] == "first" else []) + grp
-            for j in digits:
-                S = merge_digit(S, n, j)
-            if q["fuse_reduce"]:
-                S = grouped_reduce(S, n, grp + (chunk_digits if q["chunk_reduce"] else []))
-        else:
-            S = grouped_reduce(S, n, grp + (chunk_digits if q["chunk_reduce"] else []))
+    for sp in p["passes"]:
+        for ph in sp["phases"]:
+            grp = [C + d for d in range(ph["a"], ph["a"] + ph["K"])]
+            if ph["load"] == "tt":
+                for j in range(C):
+                    S = merge_digit(S, n, j)
+            if ph["merge"]:
+                for j in grp:
+                    S = merge_digit(S, n, j)
+            red = (grp if ph["reduce"] else []) + [i for i in range(C) if (ph["chunk_mask"] >> i) & 1]
+            if red:
+                S = grouped_reduce(S, n, red)
     want = oracle.sweep(n, on, dc) != 0
     assert np.array_equal(S, want)
-
-
-@pytest.mark.parametrize("n", list(range(13, 26)))
-def test_plan_rows_in_bounds(n):
-    """The highest row any tile of any pass touches is below 3^H (same index
-    formulas as the kernel, evaluated at the last tile, the largest group index
-    and the largest inner index); tile counts fit a 1-D grid."""
-    p = plan(n)
-    H = p["H"]
-    for q in p["passes"]:
-        assert 0 < q["tiles"] < 2 ** 31
-        last = q["tiles"] - 1
-        mid = last % q["n_mid"]
-        topi = last // q["n_mid"]
-        top_t = spread3(topi) if q["top_binary"] else topi
-        base = mid * 3 ** q["B"] + top_t * q["w_top"]
-        g_max = 3 ** q["K"] - 1
-        row_max = base + (3 ** q["B"] - 1) + g_max * q["w_g"]
-        assert row_max < 3 ** H
-        if q["kind"] == "first" and H > 7:
-            # truth-table words read: topi * 2^K + gb < 2^H
-            assert (topi + 1) * 2 ** q["K"] <= 2 ** H
-        if q["write_out"]:
-            # the bitmap pass covers rows 0 .. 3^H-1 contiguously
-            assert q["a"] == 0 and q["B"] == 0 and q["tiles"] * 3 ** q["K"] == 3 ** H
