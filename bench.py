@@ -215,28 +215,26 @@ def run_ours(args, rank, world, local):
     sh = stream.cuda_stream
     npass = dqmc.dqmc_plan_passes(n)
     plan = dqmc.dqmc_plan_json(n)
-    names = [f"pass{i}:{q['kind']}{'+reduce' if q['fuse_reduce'] else ''}{'+bitmap' if q['write_out'] else ''}"
-             f"(K={q['K']},B={q['B']},a={q['a']})" for i, q in enumerate(plan["passes"])]
-    names.append("compact(count+scan+emit)")
+    def pass_name(i, q):
+        ph = "+".join(f"{x['load']}" + ("M" if x["merge"] else "") + ("R" if x["reduce"] else "")
+                      + ("c" if x["chunk_mask"] else "") + ("O" if x["out"] else "")
+                      + f"[{x['a']}:{x['a'] + x['K']}|B{x['B']}]" for x in q["phases"])
+        return f"pass{i}:{ph}"
+    names = [pass_name(i, q) for i, q in enumerate(plan["passes"])]
 
     def step(events=None):
         for p in range(npass):
-            st = L.dqmc_sweep_pass_dev(n, p, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), buf.count.data_ptr(),
-                                       buf.work.data_ptr(), buf.work_bytes, sh)
+            st = L.dqmc_sweep_pass_dev(n, p, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), buf.pairs.data_ptr(),
+                                       cap, buf.count.data_ptr(), buf.work.data_ptr(), buf.work_bytes, sh)
             if st != 0:
                 raise dqmc.DqmcError(st, f"pass {p}")
             if events is not None:
                 events[p].record(stream)
-        st = L.dqmc_compact_dev(n, buf.bitmap.data_ptr(), buf.pairs.data_ptr(), cap, buf.count.data_ptr(),
-                                buf.work.data_ptr(), buf.work_bytes, sh)
-        if st != 0:
-            raise dqmc.DqmcError(st, "compact")
-        if events is not None:
-            events[npass].record(stream)
 
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
+    buf.status()
     count = int(buf.count.item())
     if count > cap:
         raise SystemExit(f"list overflow: {count} primes > cap {cap}")
@@ -244,7 +242,7 @@ def run_ours(args, rank, world, local):
     sampler = ClockSampler(local) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass)] for _ in range(K)]
     start = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -255,11 +253,12 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     barrier()
     t_wall1 = time.time()
-    total_ms = start.elapsed_time(evs[K - 1][npass])
-    per_pass = [0.0] * (npass + 1)
+    buf.status()  # raises DqmcError if a bounded device wait gave up
+    total_ms = start.elapsed_time(evs[K - 1][npass - 1])
+    per_pass = [0.0] * npass
     for k in range(K):
-        prev = start if k == 0 else evs[k - 1][npass]
-        for p in range(npass + 1):
+        prev = start if k == 0 else evs[k - 1][npass - 1]
+        for p in range(npass):
             per_pass[p] += prev.elapsed_time(evs[k][p]) if p == 0 else evs[k][p - 1].elapsed_time(evs[k][p])
     per_pass = [x / K for x in per_pass]
     ms = total_ms / K
@@ -298,8 +297,8 @@ def run_ours(args, rank, world, local):
         "path_roofline": {"b_roof_bytes": b_roof, "achieved_gbs": b_roof / (ms / 1e3) / 1e9,
                           "frac_of_peak": b_roof / (ms / 1e3) / 1e9 / peak,
                           "note": "B_roof = 2^n/8 + 3*ceil(3^n/8): read input, write merged state, read it, write primes"},
-        "per_kernel_ms": {names[p]: per_pass[p] for p in range(npass + 1)},
-        "gpu_launches": K * (npass + 3),
+        "per_kernel_ms": {names[p]: per_pass[p] for p in range(npass)},
+        "gpu_launches": K * npass,
         "clocks": clocks,
     }
 

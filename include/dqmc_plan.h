@@ -38,13 +38,25 @@ int dqmc_plan_passes(uint32_t n);
  * bytes it writes.  0 for a bad n or pass. */
 uint64_t dqmc_pass_bytes(uint32_t n, int pass, int with_dc);
 
-/* Enqueue pass `pass` alone (same arguments as dqmc_primes_dev).  Running
- * passes 0 .. dqmc_plan_passes(n)-1 in order on one stream is exactly
- * dqmc_primes_dev; pass 0 also zeroes *d_count (or the workspace counter).
- * Lets a caller put CUDA events between the kernels of the sweep. */
+/* Enqueue pass `pass` alone (arguments as dqmc_list_dev).  Running passes
+ * 0 .. dqmc_plan_passes(n)-1 in order on one stream is exactly dqmc_list_dev
+ * (d_pairs != NULL) or dqmc_primes_dev (d_pairs == NULL, cap 0); pass 0 also
+ * zeroes *d_count and the workspace's control block.  The last pass writes the
+ * bitmap, the count and (if asked) the list.  Lets a caller put CUDA events
+ * between the kernels of the sweep. */
 int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const void *d_dc,
-                        void *d_bitmap, uint64_t *d_count, void *d_work,
-                        uint64_t work_bytes, void *stream);
+                        void *d_bitmap, uint32_t *d_pairs, uint64_t cap,
+                        uint64_t *d_count, void *d_work, uint64_t work_bytes,
+                        void *stream);
+
+/* Self-test of the bounded device waits (no GPU fault, nothing hangs): zeroes
+ * the control block of d_work, then runs one device wait on a counter that no
+ * kernel ever sets, with a limit of wait_ns nanoseconds (at most 10^9).  A
+ * following dqmc_dev_status() must return DQMC_ETIMEOUT, and the next sweep
+ * on the same workspace runs normally.  n >= 13 (a workspace with a control
+ * block).  Returns DQMC_OK once enqueued. */
+int dqmc_selftest_timeout(uint32_t n, void *d_work, uint64_t work_bytes,
+                          uint64_t wait_ns, void *stream);
 
 #ifdef __cplusplus
 }

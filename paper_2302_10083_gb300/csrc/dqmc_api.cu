@@ -443,6 +443,9 @@ extern "C" uint64_t dqmc_pass_bytes(uint32_t n, int pass, int with_dc)
     return super_bytes(p, pass, with_dc != 0);
 }
 
+extern "C" int dqmc_compact_dev(uint32_t n, const void *d_bitmap, uint32_t *d_pairs, uint64_t cap,
+                                uint64_t *d_count, void *d_work, uint64_t work_bytes, void *stream);
+
 static int check_dev_args(uint32_t n, const void *d_on, const void *d_dc, const void *d_work,
                           uint64_t work_bytes)
 {
@@ -484,10 +487,28 @@ extern "C" int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc, v
 }
 
 extern "C" int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const void *d_dc, void *d_bitmap,
-                                   uint64_t *d_count, void *d_work, uint64_t work_bytes, void *stream)
+                                   uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work,
+                                   uint64_t work_bytes, void *stream)
 {
-    if (pass < 0) return DQMC_EINVAL;
-    return sweep_dev(n, pass, pass + 1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream);
+    if (pass < 0 || n > DQMC_MAX_N || (cap && !d_pairs) || (d_pairs && !aligned(d_pairs, 8))) return DQMC_EINVAL;
+    if (d_pairs && !d_count) return DQMC_EINVAL;
+    const Plan plan = make_plan((int)n);
+    if (!plan.sps.empty())
+        return sweep_dev(n, pass, pass + 1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream,
+                         cap ? d_pairs : nullptr, cap);
+    int st = sweep_dev(n, pass, pass + 1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream);
+    if (st || !d_pairs || pass != plan_passes(plan) - 1) return st;
+    return dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
+}
+
+extern "C" int dqmc_selftest_timeout(uint32_t n, void *d_work, uint64_t work_bytes, uint64_t wait_ns, void *stream)
+{
+    if (n > DQMC_MAX_N || !d_work || !aligned(d_work, 256) || wait_ns > 1000000000ull) return DQMC_EINVAL;
+    const Plan plan = make_plan((int)n);
+    const Workspace w = workspace_layout((int)n);
+    if (plan.sps.empty() || work_bytes < w.total) return DQMC_EINVAL;
+    return map_cuda(launch_selftest_wait(static_cast<char *>(d_work) + w.ctrl_off, w.ctrl_bytes, wait_ns,
+                                         static_cast<cudaStream_t>(stream)));
 }
 
 extern "C" int dqmc_compact_dev(uint32_t n, const void *d_bitmap, uint32_t *d_pairs, uint64_t cap,

@@ -140,6 +140,9 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
                          uint32_t *d_bitmap, unsigned long long *d_count, uint32_t *d_pairs,
                          uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last);
 
+// Test hook: a device wait on a counter nothing sets; it must time out.
+cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wait_ns, cudaStream_t stream);
+
 // Enqueue compaction of a dense bitmap into (mask, value) pairs.
 constexpr int kListWordsPerBlock = 4096;
 cudaError_t launch_compact(int n, const uint32_t *d_bitmap, uint32_t *d_pairs, uint64_t cap,

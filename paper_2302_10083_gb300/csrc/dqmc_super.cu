@@ -571,8 +571,8 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                                     while (bits) {
                                         const int b = __ffs(bits) - 1;
                                         bits &= bits - 1;
-                                        if (k < A.cap) {
-                                            const int q = 32 * w + b;
+                                        const int q = 32 * w + b;  // < 243: padding bits stay 0
+                                        if (k < A.cap && q < 243) {
                                             A.pairs[k] = make_uint2((rm | S.t5m[q]) & A.nmask,
                                                                     (rv | S.t5v[q]) & A.nmask);
                                         }
@@ -647,6 +647,24 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
             atomicAdd(done + sb * sp.nph + p, 1u);
         }
     }
+}
+
+// One thread waits on a phase counter that nothing increments: the bounded
+// wait must give up after wait_ns and leave kErrTimeout in the error word.
+__global__ void selftest_wait_kernel(const SweepArgs A)
+{
+    if (threadIdx.x == 0) wait_counter(A, A.ctrl + 1 + kCtrlTickets, 1u);
+}
+
+cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wait_ns, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(d_ctrl, 0, ctrl_bytes, stream);
+    if (e != cudaSuccess) return e;
+    SweepArgs a{};
+    a.ctrl = static_cast<uint32_t *>(d_ctrl);
+    a.wait_ns = wait_ns;
+    selftest_wait_kernel<<<1, 32, 0, stream>>>(a);
+    return cudaGetLastError();
 }
 
 static int occupancy_blocks(size_t smem)

@@ -59,8 +59,9 @@ _SIGS = {
     "dqmc_plan_passes": (ctypes.c_int, [ctypes.c_uint32]),
     "dqmc_dev_status": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_pass_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int, ctypes.c_int]),
-    "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp,
-                                           ctypes.c_uint64, c_vp]),
+    "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
+                                           ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
+    "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
 }
 
 
@@ -188,9 +189,16 @@ def dqmc_primes_dev(n, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream
                                         stream or None), "dqmc_primes_dev")
 
 
-def dqmc_sweep_pass_dev(n, pass_index, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream) -> int:
-    return _check(lib().dqmc_sweep_pass_dev(n, pass_index, d_on, d_dc or None, d_bitmap, d_count or None, d_work,
-                                            work_bytes, stream or None), "dqmc_sweep_pass_dev")
+def dqmc_sweep_pass_dev(n, pass_index, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes,
+                        stream) -> int:
+    return _check(lib().dqmc_sweep_pass_dev(n, pass_index, d_on, d_dc or None, d_bitmap, d_pairs or None, cap,
+                                            d_count or None, d_work, work_bytes, stream or None),
+                  "dqmc_sweep_pass_dev")
+
+
+def dqmc_selftest_timeout(n, d_work, work_bytes, wait_ns, stream) -> int:
+    return _check(lib().dqmc_selftest_timeout(n, d_work, work_bytes, wait_ns, stream or None),
+                  "dqmc_selftest_timeout")
 
 
 def dqmc_list_dev(n, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:

@@ -160,7 +160,51 @@ def test_repeat_calls_identical():
     assert np.array_equal(dqmc.dqmc_primes(n, b), rb)
 
 
-# ------------------------------------------------------------ n = 24 sampled
+def test_n21_three_phase_pass_bit_exact():
+    """n = 21 is the smallest n whose Merge/Reduce pass over the top digits runs
+    three phases on L2-resident super-blocks: bit-exact against the byte oracle."""
+    on, dc = synth.random_function(21, 6, 0.8, 0.05)
+    check_all(21, on, dc)
+
+
+def test_per_pass_entry_points_match():
+    """dqmc_sweep_pass_dev over all passes equals dqmc_list_dev."""
+    n = 17
+    on, _ = synth.random_function(n, 12, 0.7)
+    S = oracle.sweep(n, on)
+    want_bm, want_pairs = oracle.bitmap(n, S), oracle.pairs(n, S)
+    buf = dqmc.DeviceBuffers(n, cap=len(want_pairs))
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    sh = torch.cuda.current_stream().cuda_stream
+    for p in range(dqmc.dqmc_plan_passes(n)):
+        dqmc.dqmc_sweep_pass_dev(n, p, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), buf.pairs.data_ptr(),
+                                 buf.cap, buf.count.data_ptr(), buf.work.data_ptr(), buf.work_bytes, sh)
+    buf.status()
+    assert np.array_equal(buf.bitmap[: want_bm.size].cpu().numpy(), want_bm)
+    assert int(buf.count.item()) == len(want_pairs)
+    got = buf.pairs[: 2 * len(want_pairs)].cpu().numpy().view(np.uint32).reshape(-1, 2)
+    assert np.array_equal(got, want_pairs)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a counter nothing sets gives up (50 ms limit) and the
+    host reads DQMC_ETIMEOUT; the same workspace then sweeps normally."""
+    n = 14
+    on, _ = synth.random_function(n, 3, 0.8)
+    buf = dqmc.DeviceBuffers(n, cap=1 << 20)
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    sh = torch.cuda.current_stream().cuda_stream
+    dqmc.dqmc_selftest_timeout(n, buf.work.data_ptr(), buf.work_bytes, 50_000_000, sh)
+    with pytest.raises(dqmc.DqmcError) as ei:
+        buf.status()
+    assert ei.value.status == dqmc.DQMC_ETIMEOUT
+    buf.list()
+    buf.status()
+    S = oracle.sweep(n, on)
+    assert np.array_equal(buf.bitmap[: (3 ** n + 7) // 8].cpu().numpy(), oracle.bitmap(n, S))
+
+
+# ------------------------------------------------------ large n, sampled
 
 def _sample_bits(bitmap_dev, rhos):
     idx = torch.from_numpy((rhos >> 3).astype(np.int64)).to(bitmap_dev.device)
@@ -168,48 +212,57 @@ def _sample_bits(bitmap_dev, rhos):
     return ((bytes_ >> (rhos & 7).astype(np.uint8)) & 1).astype(bool)
 
 
-def test_n24_workload_sampled():
-    """n = 24, ON ~ Bernoulli(0.85), seed 1, in the launch configuration the
-    benchmark times (device API, list included): every sampled listed prime is
-    prime by definition, sampled cells agree with the pointwise oracle, the list
-    is ascending and matches the bitmap, and the count is within 1% of its
-    expectation."""
-    n = 24
-    on, _ = synth.single_n24(1)
-    expected = bf.expected_primes(n, 0.85)
-    cap = int(expected * 1.05)
-    buf = dqmc.DeviceBuffers(n, with_dc=False, cap=cap)
+def sampled_check(n, on, dc, p_support, n_list=20000, n_cells=200000, seed=24):
+    """Sweep + list in the benchmark's launch configuration (device API), then:
+    every sampled listed prime is prime by definition and set in the bitmap, the
+    list is ascending, sampled cells agree with the pointwise oracle, the two
+    independent counts agree, and the count is within 1% of its expectation."""
+    expected = bf.expected_primes(n, p_support)
+    cap = int(expected * 1.05) + 4096
+    buf = dqmc.DeviceBuffers(n, with_dc=dc is not None, cap=cap)
     buf.on[: on.size].copy_(torch.from_numpy(on))
+    if dc is not None:
+        buf.dc[: dc.size].copy_(torch.from_numpy(dc))
     buf.list()
-    torch.cuda.synchronize()
+    buf.status()
     count = int(buf.count.item())
     assert abs(count - expected) / expected < 0.01
     assert count <= cap
-    rng = np.random.default_rng(24)
-    k = np.unique(rng.integers(0, count, size=20000))
+    rng = np.random.default_rng(seed)
+    k = np.unique(rng.integers(0, count, size=n_list))
     pairs = buf.pairs.view(-1, 2)[torch.from_numpy(k).cuda()].cpu().numpy().view(np.uint32)
-    # rho of each listed cube from (mask, value)
     rho = np.zeros(len(k), dtype=np.int64)
     for i in range(n):
         d = np.where(((pairs[:, 0] >> i) & 1) == 0, 2, (pairs[:, 1] >> i) & 1).astype(np.int64)
         rho += d * 3 ** i
-    assert np.all(np.diff(rho) > 0)                       # ascending
-    assert np.all(_sample_bits(buf.bitmap, rho))          # in the bitmap
-    assert np.all(oracle.is_prime_many(n, on, None, rho))  # prime by definition
-    cells = rng.integers(0, 3 ** n, size=200000, dtype=np.int64)
-    got = _sample_bits(buf.bitmap, cells)
-    want = oracle.is_prime_many(n, on, None, cells)
-    assert np.array_equal(got, want)
-    # the sweep's own popcount (bitmap pass) equals the compaction's count
+    assert np.all(np.diff(rho) > 0)
+    assert np.all(_sample_bits(buf.bitmap, rho))
+    assert np.all(oracle.is_prime_many(n, on, dc, rho))
+    cells = rng.integers(0, 3 ** n, size=n_cells, dtype=np.int64)
+    assert np.array_equal(_sample_bits(buf.bitmap, cells), oracle.is_prime_many(n, on, dc, cells))
+    # the sweep's own popcount (bitmap pass, no list) equals the list's count
     c2 = torch.zeros(1, dtype=torch.int64, device="cuda")
-    dqmc.dqmc_primes_dev(n, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), c2.data_ptr(),
-                         buf.work.data_ptr(), buf.work_bytes, torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
+    dqmc.dqmc_primes_dev(n, buf.on.data_ptr(), buf.dc.data_ptr() if dc is not None else None,
+                         buf.bitmap.data_ptr(), c2.data_ptr(), buf.work.data_ptr(), buf.work_bytes,
+                         torch.cuda.current_stream().cuda_stream)
+    buf.status()
     assert int(c2.item()) == count
-    # padding bits are zero
-    bm = buf.bitmap
     nb = dqmc.dqmc_bitmap_bytes(n)
     tail_bits = 3 ** n - 8 * (nb - 1)
-    last = int(bm[nb - 1].item())
-    assert last >> tail_bits == 0
-    assert not bm[nb:].any().item()
+    assert int(buf.bitmap[nb - 1].item()) >> tail_bits == 0
+    assert not buf.bitmap[nb:].any().item()
+    del buf
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [22, 23])
+def test_large_n_sampled(n):
+    on, dc = synth.random_function(n, 2, 0.8, 0.05)
+    p_sup = 0.8 + 0.2 * 0.05
+    sampled_check(n, on, dc, p_sup, n_list=5000, n_cells=50000)
+
+
+def test_n24_workload_sampled():
+    """n = 24, ON ~ Bernoulli(0.85), seed 1 (the benchmark workload)."""
+    on, _ = synth.single_n24(1)
+    sampled_check(24, on, None, 0.85)
