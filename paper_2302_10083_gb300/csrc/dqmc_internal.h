@@ -134,6 +134,8 @@ CtrlLayout ctrl_layout(const Plan &p);
 
 // Status word written by a timed-out device wait (dqmc_dev_status reads it).
 constexpr uint32_t kErrTimeout = 0x54494d45u;  // "TIME"
+// Status word of the checked build when an index fell outside its buffer.
+constexpr uint32_t kErrBounds = 0x424f554eu;   // "BOUN"
 
 // Enqueue the super-passes of a plan (n >= 13).  d_pairs may be null (no list).
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,

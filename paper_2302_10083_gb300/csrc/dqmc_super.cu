@@ -28,6 +28,9 @@
 //          (funnel-shifted rows combined in shared memory), the count, and
 //          the (mask, value) list placed by a decoupled look-back over the
 //          bitmap tiles in rho order.
+#include <cstdio>
+#include <cstdlib>
+
 #include "dqmc_chunk.cuh"
 #include "dqmc_internal.h"
 
@@ -72,7 +75,30 @@ struct SweepArgs {
     uint64_t wait_ns;           // bound of every device wait
     uint32_t nmask;             // (1 << n) - 1
     int H;
+    // buffer sizes, checked in the DQMC_CHECKED build
+    uint64_t state_rows, tt_words, out_tiles, ctrl_words;
+    int l2_discard;             // drop dead state lines from L2 in the bitmap phase
 };
+
+// Checked build (environment DQMC_CHECKED=1): every global and shared index is
+// compared with its buffer before the access; a bad one is reported (printf,
+// error word kErrBounds) and the access is skipped, so nothing faults.
+enum CheckWhat : int { kChkTT = 1, kChkTile, kChkState, kChkDiscard, kChkCtrl, kChkStatus, kChkStage, kChkOut,
+                       kChkTable };
+template <bool kCheck>
+__device__ __forceinline__ bool ck(const SweepArgs &A, bool cond, int what, uint64_t idx, uint64_t lim)
+{
+    if constexpr (!kCheck) {
+        return true;
+    } else {
+        if (cond) return true;
+        atomicCAS(A.ctrl, 0u, kErrBounds);
+        if (atomicAdd(A.ctrl + kCtrlTickets, 1u) < 16u)   // spare ticket slot counts reports
+            printf("dqmc checked: what=%d idx=%llu lim=%llu block=%d thread=%d\n", what,
+                   (unsigned long long)idx, (unsigned long long)lim, (int)blockIdx.x, (int)threadIdx.x);
+        return false;
+    }
+}
 
 constexpr int kSThreads = 256;
 constexpr int kRounds = (kTileRowsMax + kSThreads - 1) / kSThreads;  // 3
@@ -233,8 +259,13 @@ __device__ __forceinline__ bool wait_counter(const SweepArgs &A, const uint32_t 
 
 // Decoupled look-back over the bitmap tiles (warp 0).  Returns the number of
 // primes in tiles 0..T-1; publishes this tile's inclusive prefix.
+template <bool kCheck>
 __device__ unsigned long long lookback(const SweepArgs &A, uint64_t T, unsigned long long count, bool &ok)
 {
+    if (!ck<kCheck>(A, T < A.out_tiles, kChkStatus, T, A.out_tiles)) {
+        ok = false;
+        return 0;
+    }
     const int lane = threadIdx.x & 31;
     ok = true;
     if (T == 0) {
@@ -289,8 +320,10 @@ struct TileShared {
     int abort;
 };
 
+template <bool kCheck>
 __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPassDesc sp, const SweepArgs A)
 {
+    constexpr uint32_t kSlots = 2 * kTileRowsMax;
     extern __shared__ uint4 tile[];
     __shared__ TileShared S;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -335,7 +368,9 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) S.ticket = atomicAdd(tickets + sp.slot, 1u);
+        if (tid == 0)
+            S.ticket = ck<kCheck>(A, sp.slot < kCtrlTickets - 1, kChkCtrl, sp.slot, kCtrlTickets - 1)
+                           ? atomicAdd(tickets + sp.slot, 1u) : 0xffffffffu;
         __syncthreads();
         const uint64_t ticket = S.ticket;
         if (ticket >= total) break;
@@ -350,12 +385,16 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
 
         if (p > 0) {
             if (tid == 0) {
-                S.abort = !wait_counter(A, done + sb * sp.nph + (p - 1), sp.ph[p - 1].tiles);
+                const uint64_t di = sp.done_off + sb * sp.nph + (p - 1);
+                S.abort = !ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words) ||
+                          !wait_counter(A, done + sb * sp.nph + (p - 1), sp.ph[p - 1].tiles);
                 __threadfence();
             }
             __syncthreads();
             if (S.abort) {
-                if (tid == 0) atomicAdd(done + sb * sp.nph + p, 1u);
+                const uint64_t di = sp.done_off + sb * sp.nph + p;
+                if (tid == 0 && ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words))
+                    atomicAdd(done + sb * sp.nph + p, 1u);
                 continue;
             }
         }
@@ -369,11 +408,16 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
         // ---------------------------------------------------------------- load
         if (ph.load == kLoadTT) {
             for (uint32_t gb = tid; gb < NB; gb += kSThreads) {
+                if (!ck<kCheck>(A, ttb + gb < A.tt_words, kChkTT, ttb + gb, A.tt_words)) continue;
+                if (!ck<kCheck>(A, gb < 64, kChkTable, gb, 64)) continue;
                 uint32_t x = __ldg(A.on + ttb + gb);
                 if (A.dc) x |= __ldg(A.dc + ttb + gb);
                 uint32_t v[kChunkWords];
                 chunk_from_word(x, v);
                 const int r = S.sp3[gb];
+                if (!ck<kCheck>(A, (uint32_t)slot_s(r, 1) < kSlots && (uint32_t)slot_s(r, 0) < kSlots, kChkTile, r,
+                                kTileRowsMax))
+                    continue;
                 tile[slot_s(r, 0)] = make_uint4(v[0], v[1], v[2], v[3]);
                 tile[slot_s(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
             }
@@ -383,8 +427,12 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                 const uint32_t ri = pc >> 1;
                 const uint32_t gb = div_pow3(ri, B);
                 const uint32_t e = ri - gb * RE;
+                if (!ck<kCheck>(A, gb < 64, kChkTable, gb, 64)) continue;
                 const uint32_t g = S.sp3[gb];
                 const uint64_t row = base + e + (uint64_t)g * w_g;
+                if (!ck<kCheck>(A, (uint32_t)slot_s(g * RE + e, h) < kSlots, kChkTile, g * RE + e, kTileRowsMax))
+                    continue;
+                if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
                 cp_async16s(&tile[slot_s(g * RE + e, h)], &A.state[2 * row + h]);
             }
             asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -395,18 +443,23 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                 const uint32_t g = div_pow3(ri, B);
                 const uint32_t e = ri - g * RE;
                 const uint64_t row = base + e + (uint64_t)g * w_g;
+                if (!ck<kCheck>(A, (uint32_t)slot_s(ri, h) < kSlots, kChkTile, ri, kTileRowsMax)) continue;
+                if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
                 cp_async16s(&tile[slot_s(ri, h)], &A.state[2 * row + h]);
             }
             asm volatile("cp.async.wait_all;\n" ::: "memory");
         }
         __syncthreads();
-        if (ph.out) {
+        if (ph.out && A.l2_discard) {
             // The bitmap phase is the last reader of these rows: drop their
-            // lines from L2 without writing them back.
+            // lines from L2 without writing them back (off unless
+            // DQMC_L2_DISCARD=1).
             const uint64_t b0 = base * kChunkBytes, b1 = (base + R) * kChunkBytes;
             const uint64_t l0 = (b0 + 127) / 128, l1 = b1 / 128;
             const char *st = reinterpret_cast<const char *>(A.state);
-            for (uint64_t l = l0 + tid; l < l1; l += kSThreads) discard_l2(st + l * 128);
+            for (uint64_t l = l0 + tid; l < l1; l += kSThreads)
+                if (ck<kCheck>(A, (l + 1) * 128 <= A.state_rows * kChunkBytes, kChkDiscard, l, A.state_rows / 4))
+                    discard_l2(st + l * 128);
         }
 
         // --------------------------------------------------------------- Merge
@@ -421,8 +474,10 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                     const uint32_t e = r - q * RE;
                     const uint32_t hb = div_pow3(q, j);
                     const uint32_t lo = q - hb * dj;
+                    if (!ck<kCheck>(A, hb < 64, kChkTable, hb, 64)) continue;
                     const uint32_t g = lo + 3 * dj * S.sp3[hb];
                     const int r0 = g * RE + e;
+                    if (!ck<kCheck>(A, (uint32_t)(r0 + 2 * dj * RE) < R, kChkTile, r0 + 2 * dj * RE, R)) continue;
                     const uint4 s0 = tile[slot_s(r0, h)];
                     const uint4 s1 = tile[slot_s(r0 + dj * RE, h)];
                     tile[slot_s(r0 + 2 * dj * RE, h)] = make_uint4(s0.x & s1.x, s0.y & s1.y, s0.z & s1.z, s0.w & s1.w);
@@ -441,9 +496,11 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                 const int h = pc & 1;
                 const uint32_t ri = pc >> 1;
                 const uint32_t g = div_pow3(ri, B);
+                if (!ck<kCheck>(A, g < (uint32_t)kTileRowsMax, kChkTable, g, kTileRowsMax)) continue;
                 if (!all && !S.has_star[g]) continue;
                 const uint32_t e = ri - g * RE;
                 const uint64_t row = base + e + (uint64_t)g * w_g;
+                if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
                 A.state[2 * row + h] = tile[slot_s(ri, h)];
             }
         } else {
@@ -466,7 +523,7 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                             const uint32_t q = gg / 3u;
                             const uint32_t dg = gg - 3u * q;
                             gg = q;
-                            if (dg != 2) {
+                            if (dg != 2 && ck<kCheck>(A, ri + (2 - dg) * wgt < R, kChkTile, ri + (2 - dg) * wgt, R)) {
                                 const int nb = ri + (2 - dg) * wgt;
                                 const uint4 a0 = tile[slot_s(nb, 0)], a1 = tile[slot_s(nb, 1)];
                                 acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
@@ -493,6 +550,7 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                         const uint32_t g = div_pow3(ri, B);
                         const uint32_t e = ri - g * RE;
                         const uint64_t row = base + e + (uint64_t)g * w_g;
+                        if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
                         A.state[2 * row] = make_uint4(res[rd][0], res[rd][1], res[rd][2], res[rd][3]);
                         A.state[2 * row + 1] = make_uint4(res[rd][4], res[rd][5], res[rd][6], res[rd][7]);
                     }
@@ -522,7 +580,7 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                     const uint64_t T = base / kTileRowsMax;
                     if (wid == 0) {
                         bool ok;
-                        const unsigned long long ex = lookback(A, T, tile_total, ok);
+                        const unsigned long long ex = lookback<kCheck>(A, T, tile_total, ok);
                         if (lane == 0) {
                             S.excl = ex;
                             S.abort = !ok;
@@ -562,7 +620,7 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                             unsigned long long k = run + before + (x - rc[rd]);
                             run += all;
                             const uint32_t ri = rd * kSThreads + tid;
-                            if (rc[rd] && k < A.cap) {
+                            if (rc[rd] && k < A.cap && ck<kCheck>(A, ri < (uint32_t)kTileRowsMax, kChkTable, ri, kTileRowsMax)) {
                                 const uint32_t rm = S.tile_mask | ((uint32_t)S.m6[ri] << 5);
                                 const uint32_t rv = S.tile_val | ((uint32_t)S.v6[ri] << 5);
 #pragma unroll
@@ -594,7 +652,8 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                 const uint64_t W0 = bit0 >> 5;
                 const uint32_t L = R * 243u;
                 const uint32_t nw = (o + L + 31) >> 5;
-                for (uint32_t i = tid; i < nw; i += kSThreads) stg[i] = 0u;
+                ck<kCheck>(A, nw <= kSlots * 4, kChkStage, nw, kSlots * 4);
+                for (uint32_t i = tid; i < nw && i < kSlots * 4; i += kSThreads) stg[i] = 0u;
                 __syncthreads();
 #pragma unroll
                 for (int rd = 0; rd < kRounds; ++rd) {
@@ -603,6 +662,7 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                         const uint32_t lb = o + 243u * ri;
                         const uint32_t k0 = lb >> 5, s = lb & 31;
                         const uint32_t c = (s + 243u + 31u) >> 5;  // 8 or 9 words
+                        if (!ck<kCheck>(A, k0 + c <= kSlots * 4, kChkStage, k0 + c, kSlots * 4)) continue;
                         uint32_t w8[9];
                         w8[0] = res[rd][0] << s;
 #pragma unroll
@@ -625,6 +685,8 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
                     const bool shared_prev = (i == 0 && o != 0);
                     const bool shared_next = (i == nw - 1 && !last_tile && tail != 0);
                     uint32_t *dst = A.out + W0 + i;
+                    if (!ck<kCheck>(A, W0 + i < A.out_alloc_words && i < kSlots * 4, kChkOut, W0 + i, A.out_alloc_words))
+                        continue;
                     if (!shared_prev && !shared_next) {
                         *dst = val;
                     } else {
@@ -644,7 +706,8 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            atomicAdd(done + sb * sp.nph + p, 1u);
+            const uint64_t di = sp.done_off + sb * sp.nph + p;
+            if (ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words)) atomicAdd(done + sb * sp.nph + p, 1u);
         }
     }
 }
@@ -675,7 +738,7 @@ static int occupancy_blocks(size_t smem)
     if (dev != cached_dev) {
         cudaDeviceGetAttribute(&cached_sms, cudaDevAttrMultiProcessorCount, dev);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, super_pass_kernel, kSThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, super_pass_kernel<false>, kSThreads, smem);
         cached_blocks = b > 0 ? b : 1;
         cached_dev = dev;
     }
@@ -694,7 +757,16 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
         if (e != cudaSuccess) return e;
     }
     const size_t smem = (size_t)kTileRowsMax * kChunkBytes;
-    e = cudaFuncSetAttribute(super_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const bool checked = [] {
+        const char *v = getenv("DQMC_CHECKED");
+        return v && v[0] == '1';
+    }();
+    static const bool discard = [] {
+        const char *v = getenv("DQMC_L2_DISCARD");
+        return v && v[0] == '1';
+    }();
+    auto kern = checked ? super_pass_kernel<true> : super_pass_kernel<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SweepArgs a{};
     a.on = static_cast<const uint32_t *>(d_on);
@@ -712,13 +784,18 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
     a.wait_ns = 1000000000ull;
     a.nmask = (uint32_t)((1ull << plan.n) - 1);
     a.H = plan.H;
+    a.state_rows = plan.state_rows;
+    a.tt_words = ((1ull << plan.n) + 31) / 32;
+    a.out_tiles = plan.out_tiles;
+    a.ctrl_words = cl.bytes / 4;
+    a.l2_discard = discard ? 1 : 0;
     const int resident = occupancy_blocks(smem);
     for (int i = first; i < last; ++i) {
         const SuperPassDesc &sp = plan.sps[i];
         uint64_t tickets = 0;
         for (int p = 0; p < sp.nph; ++p) tickets += (uint64_t)sp.ph[p].tiles * sp.n_sb;
         const uint64_t grid = tickets < (uint64_t)resident ? tickets : (uint64_t)resident;
-        super_pass_kernel<<<(unsigned)grid, kSThreads, smem, stream>>>(sp, a);
+        kern<<<(unsigned)grid, kSThreads, smem, stream>>>(sp, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
