@@ -175,7 +175,8 @@ __device__ __forceinline__ uint64_t step_offset(const SuperPassDesc &sp, uint64_
     return off;
 }
 
-__device__ void decode_ticket(const SuperPassDesc &sp, uint64_t ticket, int &phase, uint64_t &sb, uint32_t &tile)
+__device__ __forceinline__ void decode_ticket(const SuperPassDesc &sp, uint64_t ticket, int &phase, uint64_t &sb,
+                                              uint32_t &tile)
 {
     const uint64_t groups = (sp.n_sb + sp.window - 1) / sp.window;
     uint64_t lo = 0, hi = groups + sp.nph - 1;  // step_offset(hi) = total > ticket
@@ -260,7 +261,8 @@ __device__ __forceinline__ bool wait_counter(const SweepArgs &A, const uint32_t 
 // Decoupled look-back over the bitmap tiles (warp 0).  Returns the number of
 // primes in tiles 0..T-1; publishes this tile's inclusive prefix.
 template <bool kCheck>
-__device__ unsigned long long lookback(const SweepArgs &A, uint64_t T, unsigned long long count, bool &ok)
+__device__ __forceinline__ unsigned long long lookback(const SweepArgs &A, uint64_t T, unsigned long long count,
+                                                       bool &ok)
 {
     if (!ck<kCheck>(A, T < A.out_tiles, kChkStatus, T, A.out_tiles)) {
         ok = false;
@@ -321,12 +323,29 @@ struct TileShared {
 };
 
 template <bool kCheck>
-__global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPassDesc sp, const SweepArgs A)
+__global__ void __launch_bounds__(kSThreads, 3)
+super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_constant__ SweepArgs A_param)
 {
     constexpr uint32_t kSlots = 2 * kTileRowsMax;
     extern __shared__ uint4 tile[];
     __shared__ TileShared S;
+    // The descriptors are read with run-time indexes (phase, digit); keep one
+    // copy per CTA in shared memory and index that, not the parameter space.
+    __shared__ SuperPassDesc s_sp;
+    __shared__ SweepArgs s_A;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    {
+        static_assert(sizeof(SuperPassDesc) % 4 == 0 && sizeof(SweepArgs) % 4 == 0, "word copy");
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&sp_param);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&s_sp);
+        for (int i = tid; i < (int)(sizeof(SuperPassDesc) / 4); i += kSThreads) dst[i] = src[i];
+        const uint32_t *srcA = reinterpret_cast<const uint32_t *>(&A_param);
+        uint32_t *dstA = reinterpret_cast<uint32_t *>(&s_A);
+        for (int i = tid; i < (int)(sizeof(SweepArgs) / 4); i += kSThreads) dstA[i] = srcA[i];
+    }
+    __syncthreads();
+    const SuperPassDesc &sp = s_sp;
+    const SweepArgs &A = s_A;
 
     for (int i = tid; i < 64; i += kSThreads) {
         uint32_t r = 0, w = 1, x = i;
@@ -714,7 +733,7 @@ __global__ void __launch_bounds__(kSThreads, 3) super_pass_kernel(const SuperPas
 
 // One thread waits on a phase counter that nothing increments: the bounded
 // wait must give up after wait_ns and leave kErrTimeout in the error word.
-__global__ void selftest_wait_kernel(const SweepArgs A)
+__global__ void selftest_wait_kernel(const __grid_constant__ SweepArgs A)
 {
     if (threadIdx.x == 0) wait_counter(A, A.ctrl + 1 + kCtrlTickets, 1u);
 }
