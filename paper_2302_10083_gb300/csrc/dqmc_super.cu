@@ -75,14 +75,14 @@ struct SweepArgs {
     uint64_t wait_ns;           // bound of every device wait
     uint32_t nmask;             // (1 << n) - 1
     int H;
-    // buffer sizes, checked in the DQMC_CHECKED build
+    // buffer sizes for the bounds checks
     uint64_t state_rows, tt_words, out_tiles, ctrl_words;
     int l2_discard;             // drop dead state lines from L2 in the bitmap phase
 };
 
-// Checked build (environment DQMC_CHECKED=1): every global and shared index is
-// compared with its buffer before the access; a bad one is reported (printf,
-// error word kErrBounds) and the access is skipped, so nothing faults.
+// Bounds checks: every global and shared index is compared with its buffer
+// before the access; a bad one is reported (printf, error word kErrBounds) and
+// the access is skipped, so an index error cannot fault the GPU.
 enum CheckWhat : int { kChkTT = 1, kChkTile, kChkState, kChkDiscard, kChkCtrl, kChkStatus, kChkStage, kChkOut,
                        kChkTable };
 template <bool kCheck>
@@ -315,13 +315,37 @@ struct TileShared {
     uint8_t has_star[kTileRowsMax]; // group index has a '*' digit
     uint8_t m6[kTileRowsMax], v6[kTileRowsMax];  // mask / value bits of the 6 low high digits
     uint8_t t5m[243], t5v[243];     // mask / value bits of the 5 chunk digits
-    unsigned long long warp_sum[kSThreads / 32];
-    unsigned long long excl;
+    uint32_t warp_tot[kRounds][kSThreads / 32];  // per round: inclusive warp totals of row counts
+    // the current tile, decoded by thread 0
+    uint64_t base, ttb, sb;
+    unsigned long long excl;        // primes in the bitmap tiles before this one
     uint32_t tile_mask, tile_val;   // mask / value bits of the digits above the bitmap tile
-    uint32_t ticket;
-    int abort;
+    uint32_t t;
+    int p, abort, stop, list_ok;
 };
 
+// Mixed-radix decode of x over a list of fixed digits (first entry least
+// significant), 32-bit digit arithmetic.
+__device__ __forceinline__ void decode_fixed32(const FixedDigits &f, uint32_t x, uint64_t &row, uint64_t &tt)
+{
+    for (int i = 0; i < f.n; ++i) {
+        uint32_t d;
+        if (f.r[i] == 2) {
+            d = x & 1u;
+            x >>= 1;
+        } else {
+            const uint32_t q = x / 3u;
+            d = x - 3u * q;
+            x = q;
+        }
+        row += (uint64_t)d * f.w3[i];
+        tt += (uint64_t)d * f.w2[i];
+    }
+}
+
+// The kernel bounds-checks every global and shared index (ck): an index
+// outside its buffer is reported and the access skipped, so the kernel cannot
+// fault on one.
 template <bool kCheck>
 __global__ void __launch_bounds__(kSThreads, 3)
 super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_constant__ SweepArgs A_param)
@@ -343,10 +367,6 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
         uint32_t *dstA = reinterpret_cast<uint32_t *>(&s_A);
         for (int i = tid; i < (int)(sizeof(SweepArgs) / 4); i += kSThreads) dstA[i] = srcA[i];
     }
-    __syncthreads();
-    const SuperPassDesc &sp = s_sp;
-    const SweepArgs &A = s_A;
-
     for (int i = tid; i < 64; i += kSThreads) {
         uint32_t r = 0, w = 1, x = i;
         while (x) {
@@ -380,44 +400,60 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
         S.t5m[i] = (uint8_t)m;
         S.t5v[i] = (uint8_t)v;
     }
+    __syncthreads();
+    const SuperPassDesc &sp = s_sp;
+    const SweepArgs &A = s_A;
 
     const uint64_t total = total_tickets(sp);
     uint32_t *const tickets = A.ctrl + 1;
     uint32_t *const done = A.ctrl + sp.done_off;
+    const bool slot_ok = ck<kCheck>(A, sp.slot < kCtrlTickets - 1, kChkCtrl, sp.slot, kCtrlTickets - 1);
+    // Thread 0 holds the next ticket: it is taken while the current tile runs.
+    uint32_t next = 0xffffffffu;
+    if (tid == 0 && slot_ok) next = atomicAdd(tickets + sp.slot, 1u);
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0)
-            S.ticket = ck<kCheck>(A, sp.slot < kCtrlTickets - 1, kChkCtrl, sp.slot, kCtrlTickets - 1)
-                           ? atomicAdd(tickets + sp.slot, 1u) : 0xffffffffu;
-        __syncthreads();
-        const uint64_t ticket = S.ticket;
-        if (ticket >= total) break;
-        int p;
-        uint64_t sb;
-        uint32_t t;
-        decode_ticket(sp, ticket, p, sb, t);
-        const PhaseDesc &ph = sp.ph[p];
-        uint64_t base = 0, ttb = 0;
-        decode_fixed(sp.sb, sb, base, ttb);
-        decode_fixed(ph.fix, t, base, ttb);
-
-        if (p > 0) {
-            if (tid == 0) {
-                const uint64_t di = sp.done_off + sb * sp.nph + (p - 1);
-                S.abort = !ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words) ||
-                          !wait_counter(A, done + sb * sp.nph + (p - 1), sp.ph[p - 1].tiles);
-                __threadfence();
-            }
-            __syncthreads();
-            if (S.abort) {
-                const uint64_t di = sp.done_off + sb * sp.nph + p;
-                if (tid == 0 && ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words))
-                    atomicAdd(done + sb * sp.nph + p, 1u);
-                continue;
+        if (tid == 0) {
+            const uint64_t ticket = next;
+            if (ticket >= total) {
+                S.stop = 1;
+            } else {
+                S.stop = 0;
+                next = atomicAdd(tickets + sp.slot, 1u);
+                int p;
+                uint64_t sb;
+                uint32_t t;
+                decode_ticket(sp, ticket, p, sb, t);
+                uint64_t base = 0, ttb = 0;
+                decode_fixed32(sp.sb, (uint32_t)sb, base, ttb);
+                decode_fixed32(sp.ph[p].fix, t, base, ttb);
+                S.p = p;
+                S.sb = sb;
+                S.t = t;
+                S.base = base;
+                S.ttb = ttb;
+                int abort = 0;
+                if (p > 0) {
+                    const uint64_t di = sp.done_off + sb * sp.nph + (p - 1);
+                    abort = !ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words) ||
+                            !wait_counter(A, done + sb * sp.nph + (p - 1), sp.ph[p - 1].tiles);
+                    __threadfence();
+                }
+                S.abort = abort;
             }
         }
-
+        __syncthreads();
+        if (S.stop) break;
+        const int p = S.p;
+        const uint64_t sb = S.sb;
+        const uint64_t base = S.base, ttb = S.ttb;
+        const bool signal = (p < sp.nph - 1);   // later phases of this block wait for this tile
+        if (S.abort) {
+            __syncthreads();
+            if (tid == 0 && signal) atomicAdd(done + sb * sp.nph + p, 1u);
+            continue;
+        }
+        const PhaseDesc &ph = sp.ph[p];
         const int K = ph.K, B = ph.B;
         const uint32_t RE = (uint32_t)kP3.p[B];
         const uint32_t R = (uint32_t)kP3.p[K] * RE;
@@ -440,31 +476,21 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 tile[slot_s(r, 0)] = make_uint4(v[0], v[1], v[2], v[3]);
                 tile[slot_s(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
             }
-        } else if (ph.load == kLoadSparse) {
-            for (uint32_t pc = tid; pc < NB * RE * 2; pc += kSThreads) {
-                const int h = pc & 1;
-                const uint32_t ri = pc >> 1;
-                const uint32_t gb = div_pow3(ri, B);
-                const uint32_t e = ri - gb * RE;
-                if (!ck<kCheck>(A, gb < 64, kChkTable, gb, 64)) continue;
-                const uint32_t g = S.sp3[gb];
-                const uint64_t row = base + e + (uint64_t)g * w_g;
-                if (!ck<kCheck>(A, (uint32_t)slot_s(g * RE + e, h) < kSlots, kChkTile, g * RE + e, kTileRowsMax))
-                    continue;
-                if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
-                cp_async16s(&tile[slot_s(g * RE + e, h)], &A.state[2 * row + h]);
-            }
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
         } else {
-            for (uint32_t pc = tid; pc < R * 2; pc += kSThreads) {
+            const bool sparse = (ph.load == kLoadSparse);
+            const uint32_t npc = (sparse ? NB * RE : R) * 2;
+            for (uint32_t pc = tid; pc < npc; pc += kSThreads) {
                 const int h = pc & 1;
                 const uint32_t ri = pc >> 1;
-                const uint32_t g = div_pow3(ri, B);
-                const uint32_t e = ri - g * RE;
+                const uint32_t q = div_pow3(ri, B);
+                const uint32_t e = ri - q * RE;
+                if (!ck<kCheck>(A, !sparse || q < 64, kChkTable, q, 64)) continue;
+                const uint32_t g = sparse ? S.sp3[q] : q;
+                const uint32_t srow = g * RE + e;
                 const uint64_t row = base + e + (uint64_t)g * w_g;
-                if (!ck<kCheck>(A, (uint32_t)slot_s(ri, h) < kSlots, kChkTile, ri, kTileRowsMax)) continue;
+                if (!ck<kCheck>(A, (uint32_t)slot_s(srow, h) < kSlots, kChkTile, srow, kTileRowsMax)) continue;
                 if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
-                cp_async16s(&tile[slot_s(ri, h)], &A.state[2 * row + h]);
+                cp_async16s(&tile[slot_s(srow, h)], &A.state[2 * row + h]);
             }
             asm volatile("cp.async.wait_all;\n" ::: "memory");
         }
@@ -559,9 +585,9 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                     for (int w = 0; w < kChunkWords; ++w) res[rd][w] = 0;
                 }
             }
-            __syncthreads();  // every read of the tile is done; it is scratch from here
 
             if (!ph.out) {
+                __syncthreads();  // every read of the tile is done before rows are overwritten in place
 #pragma unroll
                 for (int rd = 0; rd < kRounds; ++rd) {
                     const uint32_t ri = rd * kSThreads + tid;
@@ -577,23 +603,40 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             } else {
                 // ------------------------------------ bitmap, count and list
                 // (B = 0, a = 0: rows base .. base + R - 1, contiguous.)
-                uint32_t rc[kRounds];
-                uint32_t mine = 0;
+                // Rows in rho order are (round, thread): per round, an
+                // inclusive warp scan of the row counts and the warp totals.
+                uint32_t rc[kRounds], incl[kRounds];
 #pragma unroll
                 for (int rd = 0; rd < kRounds; ++rd) {
                     uint32_t c = 0;
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) c += __popc(res[rd][w]);
                     rc[rd] = c;
-                    mine += c;
+                    uint32_t x = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    incl[rd] = x;
+                    if (lane == 31) S.warp_tot[rd][wid] = x;
                 }
-                unsigned long long ws = mine;
-                for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
-                if (lane == 0) S.warp_sum[wid] = ws;
-                __syncthreads();
-                unsigned long long tile_total = 0;
-                for (int i = 0; i < kSThreads / 32; ++i) tile_total += S.warp_sum[i];
-                if (tid == 0 && tile_total) atomicAdd(A.count, tile_total);
+                __syncthreads();  // tile reads done; warp totals visible
+                uint32_t before[kRounds];
+                uint32_t tile_total = 0;
+#pragma unroll
+                for (int rd = 0; rd < kRounds; ++rd) {
+                    uint32_t rt = 0, bw = 0;
+#pragma unroll
+                    for (int w = 0; w < kSThreads / 32; ++w) {
+                        const uint32_t v = S.warp_tot[rd][w];
+                        rt += v;
+                        if (w < wid) bw += v;
+                    }
+                    before[rd] = tile_total + bw + incl[rd] - rc[rd];
+                    tile_total += rt;
+                }
+                if (tid == 0 && tile_total) atomicAdd(A.count, (unsigned long long)tile_total);
 
                 if (A.pairs) {
                     const uint64_t T = base / kTileRowsMax;
@@ -602,7 +645,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                         const unsigned long long ex = lookback<kCheck>(A, T, tile_total, ok);
                         if (lane == 0) {
                             S.excl = ex;
-                            S.abort = !ok;
+                            S.list_ok = ok;
                             // mask / value bits of the digits above the tile (high digits >= 6)
                             uint64_t x = T;
                             uint32_t m = 0, v = 0;
@@ -618,27 +661,12 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                         }
                     }
                     __syncthreads();
-                    if (!S.abort) {
-                        // rows in order: round 0 (rows 0..255 by thread), round 1, round 2
-                        unsigned long long run = S.excl;
+                    if (S.list_ok) {
+                        const unsigned long long ex = S.excl;
 #pragma unroll
                         for (int rd = 0; rd < kRounds; ++rd) {
-                            uint32_t x = rc[rd];
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                                if (lane >= o) x += y;
-                            }
-                            __syncthreads();
-                            if (lane == 31) S.warp_sum[wid] = x;
-                            __syncthreads();
-                            unsigned long long before = 0, all = 0;
-                            for (int i = 0; i < kSThreads / 32; ++i) {
-                                if (i < wid) before += S.warp_sum[i];
-                                all += S.warp_sum[i];
-                            }
-                            unsigned long long k = run + before + (x - rc[rd]);
-                            run += all;
                             const uint32_t ri = rd * kSThreads + tid;
+                            unsigned long long k = ex + before[rd];
                             if (rc[rd] && k < A.cap && ck<kCheck>(A, ri < (uint32_t)kTileRowsMax, kChkTable, ri, kTileRowsMax)) {
                                 const uint32_t rm = S.tile_mask | ((uint32_t)S.m6[ri] << 5);
                                 const uint32_t rv = S.tile_val | ((uint32_t)S.v6[ri] << 5);
@@ -649,10 +677,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                                         const int b = __ffs(bits) - 1;
                                         bits &= bits - 1;
                                         const int q = 32 * w + b;  // < 243: padding bits stay 0
-                                        if (k < A.cap && q < 243) {
-                                            A.pairs[k] = make_uint2((rm | S.t5m[q]) & A.nmask,
-                                                                    (rv | S.t5v[q]) & A.nmask);
-                                        }
+                                        if (k < A.cap && q < 243)
+                                            A.pairs[k] = make_uint2((rm | S.t5m[q]) & A.nmask, (rv | S.t5v[q]) & A.nmask);
                                         ++k;
                                     }
                                 }
@@ -662,24 +688,28 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 }
 
                 // Dense bitmap: rows base .. base+R-1 are bits base*243 ..
-                // (base+R)*243-1.  Each row is funnel-shifted to its bit
-                // offset in a shared-memory copy of the tile's words; words
+                // (base+R)*243-1 (words W0 .. W0+nw-1).  Each row is funnel-
+                // shifted to its bit offset in a shared-memory copy of those
+                // words (stored sh = W0 mod 4 words in, so that 16-byte
+                // groups of the copy are 16-byte groups of the bitmap); words
                 // shared by two rows are OR-ed in with shared atomics.
                 uint32_t *stg = reinterpret_cast<uint32_t *>(tile);
                 const uint64_t bit0 = base * 243u;
                 const uint32_t o = (uint32_t)(bit0 & 31);
                 const uint64_t W0 = bit0 >> 5;
+                const uint32_t sh = (uint32_t)(W0 & 3);
                 const uint32_t L = R * 243u;
                 const uint32_t nw = (o + L + 31) >> 5;
-                ck<kCheck>(A, nw <= kSlots * 4, kChkStage, nw, kSlots * 4);
-                for (uint32_t i = tid; i < nw && i < kSlots * 4; i += kSThreads) stg[i] = 0u;
+                const uint32_t nq = (nw + sh + 3) >> 2;
+                ck<kCheck>(A, nq <= kSlots, kChkStage, nq, kSlots);
+                for (uint32_t i = tid; i < nq && i < kSlots; i += kSThreads) tile[i] = make_uint4(0u, 0u, 0u, 0u);
                 __syncthreads();
 #pragma unroll
                 for (int rd = 0; rd < kRounds; ++rd) {
                     const uint32_t ri = rd * kSThreads + tid;
                     if (ri < R) {
                         const uint32_t lb = o + 243u * ri;
-                        const uint32_t k0 = lb >> 5, s = lb & 31;
+                        const uint32_t k0 = (lb >> 5) + sh, s = lb & 31;
                         const uint32_t c = (s + 243u + 31u) >> 5;  // 8 or 9 words
                         if (!ck<kCheck>(A, k0 + c <= kSlots * 4, kChkStage, k0 + c, kSlots * 4)) continue;
                         uint32_t w8[9];
@@ -699,21 +729,33 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 __syncthreads();
                 const bool last_tile = (base + R == A.total_rows);
                 const uint32_t tail = (o + L) & 31;
-                for (uint32_t i = tid; i < nw; i += kSThreads) {
-                    const uint32_t val = stg[i];
-                    const bool shared_prev = (i == 0 && o != 0);
-                    const bool shared_next = (i == nw - 1 && !last_tile && tail != 0);
-                    uint32_t *dst = A.out + W0 + i;
-                    if (!ck<kCheck>(A, W0 + i < A.out_alloc_words && i < kSlots * 4, kChkOut, W0 + i, A.out_alloc_words))
+                for (uint32_t cq = tid; cq < nq && cq < kSlots; cq += kSThreads) {
+                    // bitmap words i = 4*cq + x - sh, x = 0..3
+                    const long long i0 = (long long)(4 * cq) - (long long)sh;
+                    if (i0 >= 1 && i0 + 3 <= (long long)nw - 2) {
+                        const uint64_t wi = W0 + (uint64_t)i0;
+                        if (!ck<kCheck>(A, wi + 4 <= A.out_alloc_words, kChkOut, wi, A.out_alloc_words)) continue;
+                        *reinterpret_cast<uint4 *>(A.out + wi) = tile[cq];
                         continue;
-                    if (!shared_prev && !shared_next) {
-                        *dst = val;
-                    } else {
-                        uint32_t m = 0xffffffffu;
-                        if (shared_prev) m &= 0xffffffffu << o;
-                        if (shared_next) m &= (1u << tail) - 1u;
-                        atomicAnd(dst, val | ~m);
-                        atomicOr(dst, val & m);
+                    }
+                    for (int x = 0; x < 4; ++x) {
+                        const long long i = i0 + x;
+                        if (i < 0 || i >= (long long)nw) continue;
+                        const uint32_t val = stg[4 * cq + x];
+                        const bool shared_prev = (i == 0 && o != 0);
+                        const bool shared_next = (i == (long long)nw - 1 && !last_tile && tail != 0);
+                        const uint64_t wi = W0 + (uint64_t)i;
+                        if (!ck<kCheck>(A, wi < A.out_alloc_words, kChkOut, wi, A.out_alloc_words)) continue;
+                        uint32_t *dst = A.out + wi;
+                        if (!shared_prev && !shared_next) {
+                            *dst = val;
+                        } else {
+                            uint32_t m = 0xffffffffu;
+                            if (shared_prev) m &= 0xffffffffu << o;
+                            if (shared_next) m &= (1u << tail) - 1u;
+                            atomicAnd(dst, val | ~m);
+                            atomicOr(dst, val & m);
+                        }
                     }
                 }
                 if (last_tile)
@@ -722,12 +764,15 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
         }
 
         // ------------------------------------------------------------- signal
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            const uint64_t di = sp.done_off + sb * sp.nph + p;
-            if (ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words)) atomicAdd(done + sb * sp.nph + p, 1u);
+        if (signal) {
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const uint64_t di = sp.done_off + sb * sp.nph + p;
+                if (ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words)) atomicAdd(done + sb * sp.nph + p, 1u);
+            }
         }
+        __syncthreads();  // the shared tile and S are reused by the next ticket
     }
 }
 
@@ -757,7 +802,7 @@ static int occupancy_blocks(size_t smem)
     if (dev != cached_dev) {
         cudaDeviceGetAttribute(&cached_sms, cudaDevAttrMultiProcessorCount, dev);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, super_pass_kernel<false>, kSThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, super_pass_kernel<true>, kSThreads, smem);
         cached_blocks = b > 0 ? b : 1;
         cached_dev = dev;
     }
@@ -776,15 +821,12 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
         if (e != cudaSuccess) return e;
     }
     const size_t smem = (size_t)kTileRowsMax * kChunkBytes;
-    static const bool checked = [] {
-        const char *v = getenv("DQMC_CHECKED");
-        return v && v[0] == '1';
-    }();
+
     static const bool discard = [] {
         const char *v = getenv("DQMC_L2_DISCARD");
         return v && v[0] == '1';
     }();
-    auto kern = checked ? super_pass_kernel<true> : super_pass_kernel<false>;
+    auto kern = super_pass_kernel<true>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SweepArgs a{};
