@@ -88,6 +88,14 @@ static void finish_superpass(SuperPassDesc &sp, const std::vector<int> &sb_digit
     sp.sb = fixed_of(outer, merged_before);
     sp.n_sb = radix_product(sp.sb);
     sp.window = window ? window : (uint32_t)std::min<uint64_t>(sp.n_sb, 0xffffffffu);
+    sp.groups = (uint32_t)((sp.n_sb + sp.window - 1) / sp.window);
+    uint32_t off = 0;
+    for (int p = 0; p < sp.nph; ++p) {
+        sp.ph_off[p] = off;
+        off += sp.window * sp.ph[p].tiles;
+    }
+    sp.step_size = off;
+    sp.n_steps = sp.groups + sp.nph - 1;
 }
 
 static std::vector<int> range_digits(int lo, int hi)
@@ -251,7 +259,9 @@ std::string describe_plan(const Plan &p)
     for (size_t i = 0; i < p.sps.size(); ++i) {
         const SuperPassDesc &sp = p.sps[i];
         s += std::string(i ? "," : "") + "{\"kind\":\"super\",\"n_sb\":" + std::to_string(sp.n_sb) +
-             ",\"window\":" + std::to_string(sp.window) + ",\"sb\":" + fixed_json(sp.sb) + ",\"phases\":[";
+             ",\"window\":" + std::to_string(sp.window) + ",\"step_size\":" + std::to_string(sp.step_size) +
+             ",\"n_steps\":" + std::to_string(sp.n_steps) + ",\"groups\":" + std::to_string(sp.groups) +
+             ",\"sb\":" + fixed_json(sp.sb) + ",\"phases\":[";
         for (int k = 0; k < sp.nph; ++k) {
             const PhaseDesc &q = sp.ph[k];
             char buf[256];

@@ -76,6 +76,12 @@ struct SuperPassDesc {
     FixedDigits sb;                 // digits fixed per super-block
     uint64_t done_off = 0;          // offset (in uint32) of this pass's phase counters
     int slot = 0;                   // ticket counter index
+    // Ticket layout: n_steps pipeline steps of step_size tickets; within step
+    // k, phase p owns tickets [ph_off[p], ph_off[p] + window * tiles_p) and
+    // runs super-block group k - p (tickets of groups outside 0..groups-1, or
+    // of super-blocks past n_sb in the last group, are empty).
+    uint32_t step_size = 0, n_steps = 0, groups = 0;
+    uint32_t ph_off[kMaxPhases] = {};
 };
 
 struct Plan {

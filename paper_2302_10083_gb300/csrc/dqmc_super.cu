@@ -270,11 +270,8 @@ __device__ __forceinline__ unsigned long long lookback(const SweepArgs &A, uint6
     }
     const int lane = threadIdx.x & 31;
     ok = true;
-    if (T == 0) {
-        if (lane == 0) atomicExch(&A.status[0], kFlagP | count);
-        return 0;
-    }
-    if (lane == 0) atomicExch(&A.status[T], kFlagA | count);
+    // (this tile's aggregate, or for T = 0 its prefix, is already published)
+    if (T == 0) return 0;
     unsigned long long excl = 0;
     long long j = (long long)T - 1;
     const uint64_t t0 = globaltimer();
@@ -320,7 +317,6 @@ struct TileShared {
     uint64_t base, ttb, sb;
     unsigned long long excl;        // primes in the bitmap tiles before this one
     uint32_t tile_mask, tile_val;   // mask / value bits of the digits above the bitmap tile
-    uint32_t t;
     int p, abort, stop, list_ok;
 };
 
@@ -343,29 +339,47 @@ __device__ __forceinline__ void decode_fixed32(const FixedDigits &f, uint32_t x,
     }
 }
 
+// Ticket -> (phase, super-block, tile); false for an empty ticket.
+__device__ __forceinline__ bool decode_ticket_step(const SuperPassDesc &sp, uint32_t ticket, int &phase, uint32_t &sb,
+                                                   uint32_t &tile)
+{
+    const uint32_t step = ticket / sp.step_size;
+    uint32_t r = ticket - step * sp.step_size;
+    int p = sp.nph - 1;
+    while (p > 0 && r < sp.ph_off[p]) --p;
+    r -= sp.ph_off[p];
+    if (step < (uint32_t)p) return false;
+    const uint32_t g = step - p;
+    if (g >= sp.groups) return false;
+    const uint32_t tiles = sp.ph[p].tiles;
+    const uint32_t sbl = r / tiles;
+    const uint64_t sb64 = (uint64_t)g * sp.window + sbl;
+    if (sb64 >= sp.n_sb) return false;
+    phase = p;
+    sb = (uint32_t)sb64;
+    tile = r - sbl * tiles;
+    return true;
+}
+
 // The kernel bounds-checks every global and shared index (ck): an index
 // outside its buffer is reported and the access skipped, so the kernel cannot
 // fault on one.
 template <bool kCheck>
 __global__ void __launch_bounds__(kSThreads, 3)
-super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_constant__ SweepArgs A_param)
+super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_constant__ SweepArgs A)
 {
     constexpr uint32_t kSlots = 2 * kTileRowsMax;
     extern __shared__ uint4 tile[];
     __shared__ TileShared S;
-    // The descriptors are read with run-time indexes (phase, digit); keep one
-    // copy per CTA in shared memory and index that, not the parameter space.
+    // The pass descriptor is read with run-time indexes (phase, digit): one
+    // copy per CTA in shared memory, indexed there, not in parameter space.
     __shared__ SuperPassDesc s_sp;
-    __shared__ SweepArgs s_A;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     {
-        static_assert(sizeof(SuperPassDesc) % 4 == 0 && sizeof(SweepArgs) % 4 == 0, "word copy");
+        static_assert(sizeof(SuperPassDesc) % 4 == 0, "word copy");
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&sp_param);
         uint32_t *dst = reinterpret_cast<uint32_t *>(&s_sp);
         for (int i = tid; i < (int)(sizeof(SuperPassDesc) / 4); i += kSThreads) dst[i] = src[i];
-        const uint32_t *srcA = reinterpret_cast<const uint32_t *>(&A_param);
-        uint32_t *dstA = reinterpret_cast<uint32_t *>(&s_A);
-        for (int i = tid; i < (int)(sizeof(SweepArgs) / 4); i += kSThreads) dstA[i] = srcA[i];
     }
     for (int i = tid; i < 64; i += kSThreads) {
         uint32_t r = 0, w = 1, x = i;
@@ -402,71 +416,79 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
     }
     __syncthreads();
     const SuperPassDesc &sp = s_sp;
-    const SweepArgs &A = s_A;
 
-    const uint64_t total = total_tickets(sp);
+    const int nph = sp.nph;
+    const uint64_t total = (uint64_t)sp.n_steps * sp.step_size;
     uint32_t *const tickets = A.ctrl + 1;
     uint32_t *const done = A.ctrl + sp.done_off;
     const bool slot_ok = ck<kCheck>(A, sp.slot < kCtrlTickets - 1, kChkCtrl, sp.slot, kCtrlTickets - 1);
+    const int slot = sp.slot;
     // Thread 0 holds the next ticket: it is taken while the current tile runs.
     uint32_t next = 0xffffffffu;
-    if (tid == 0 && slot_ok) next = atomicAdd(tickets + sp.slot, 1u);
+    if (tid == 0 && slot_ok) next = atomicAdd(tickets + slot, 1u);
 
     for (;;) {
         if (tid == 0) {
-            const uint64_t ticket = next;
-            if (ticket >= total) {
-                S.stop = 1;
-            } else {
-                S.stop = 0;
-                next = atomicAdd(tickets + sp.slot, 1u);
+            int stop = 0, valid = 0, abort = 0;
+            for (;;) {
+                const uint32_t ticket = next;
+                if ((uint64_t)ticket >= total) {
+                    stop = 1;
+                    break;
+                }
+                next = atomicAdd(tickets + slot, 1u);
                 int p;
-                uint64_t sb;
-                uint32_t t;
-                decode_ticket(sp, ticket, p, sb, t);
+                uint32_t sb, t;
+                if (!decode_ticket_step(sp, ticket, p, sb, t)) continue;  // empty ticket
                 uint64_t base = 0, ttb = 0;
-                decode_fixed32(sp.sb, (uint32_t)sb, base, ttb);
+                decode_fixed32(sp.sb, sb, base, ttb);
                 decode_fixed32(sp.ph[p].fix, t, base, ttb);
                 S.p = p;
                 S.sb = sb;
-                S.t = t;
                 S.base = base;
                 S.ttb = ttb;
-                int abort = 0;
                 if (p > 0) {
-                    const uint64_t di = sp.done_off + sb * sp.nph + (p - 1);
+                    const uint64_t di = sp.done_off + (uint64_t)sb * nph + (p - 1);
                     abort = !ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words) ||
-                            !wait_counter(A, done + sb * sp.nph + (p - 1), sp.ph[p - 1].tiles);
+                            !wait_counter(A, done + (uint64_t)sb * nph + (p - 1), sp.ph[p - 1].tiles);
                     __threadfence();
                 }
-                S.abort = abort;
+                valid = 1;
+                break;
             }
+            S.stop = stop;
+            S.abort = abort;
         }
         __syncthreads();
         if (S.stop) break;
         const int p = S.p;
         const uint64_t sb = S.sb;
         const uint64_t base = S.base, ttb = S.ttb;
-        const bool signal = (p < sp.nph - 1);   // later phases of this block wait for this tile
+        const bool signal = (p < nph - 1);   // later phases of this block wait for this tile
         if (S.abort) {
             __syncthreads();
-            if (tid == 0 && signal) atomicAdd(done + sb * sp.nph + p, 1u);
+            if (tid == 0 && signal) atomicAdd(done + sb * nph + p, 1u);
             continue;
         }
-        const PhaseDesc &ph = sp.ph[p];
-        const int K = ph.K, B = ph.B;
+        // this tile's phase, in registers
+        const int K = sp.ph[p].K, B = sp.ph[p].B;
+        const int load = sp.ph[p].load, merge = sp.ph[p].merge, reduce = sp.ph[p].reduce;
+        const int chunk_mask = sp.ph[p].chunk_mask, out = sp.ph[p].out;
         const uint32_t RE = (uint32_t)kP3.p[B];
         const uint32_t R = (uint32_t)kP3.p[K] * RE;
         const uint32_t NB = 1u << K;
-        const uint64_t w_g = kP3.p[ph.a];
+        const uint64_t w_g = kP3.p[sp.ph[p].a];
+        uint4 *const state = A.state;
+        const uint64_t state_rows = A.state_rows;
 
         // ---------------------------------------------------------------- load
-        if (ph.load == kLoadTT) {
+        if (load == kLoadTT) {
+            const uint32_t *on = A.on, *dc = A.dc;
             for (uint32_t gb = tid; gb < NB; gb += kSThreads) {
                 if (!ck<kCheck>(A, ttb + gb < A.tt_words, kChkTT, ttb + gb, A.tt_words)) continue;
                 if (!ck<kCheck>(A, gb < 64, kChkTable, gb, 64)) continue;
-                uint32_t x = __ldg(A.on + ttb + gb);
-                if (A.dc) x |= __ldg(A.dc + ttb + gb);
+                uint32_t x = __ldg(on + ttb + gb);
+                if (dc) x |= __ldg(dc + ttb + gb);
                 uint32_t v[kChunkWords];
                 chunk_from_word(x, v);
                 const int r = S.sp3[gb];
@@ -477,7 +499,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 tile[slot_s(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
             }
         } else {
-            const bool sparse = (ph.load == kLoadSparse);
+            const bool sparse = (load == kLoadSparse);
             const uint32_t npc = (sparse ? NB * RE : R) * 2;
             for (uint32_t pc = tid; pc < npc; pc += kSThreads) {
                 const int h = pc & 1;
@@ -489,26 +511,26 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 const uint32_t srow = g * RE + e;
                 const uint64_t row = base + e + (uint64_t)g * w_g;
                 if (!ck<kCheck>(A, (uint32_t)slot_s(srow, h) < kSlots, kChkTile, srow, kTileRowsMax)) continue;
-                if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
-                cp_async16s(&tile[slot_s(srow, h)], &A.state[2 * row + h]);
+                if (!ck<kCheck>(A, row < state_rows, kChkState, row, state_rows)) continue;
+                cp_async16s(&tile[slot_s(srow, h)], &state[2 * row + h]);
             }
             asm volatile("cp.async.wait_all;\n" ::: "memory");
         }
         __syncthreads();
-        if (ph.out && A.l2_discard) {
+        if (out && A.l2_discard) {
             // The bitmap phase is the last reader of these rows: drop their
             // lines from L2 without writing them back (off unless
             // DQMC_L2_DISCARD=1).
             const uint64_t b0 = base * kChunkBytes, b1 = (base + R) * kChunkBytes;
             const uint64_t l0 = (b0 + 127) / 128, l1 = b1 / 128;
-            const char *st = reinterpret_cast<const char *>(A.state);
+            const char *st = reinterpret_cast<const char *>(state);
             for (uint64_t l = l0 + tid; l < l1; l += kSThreads)
-                if (ck<kCheck>(A, (l + 1) * 128 <= A.state_rows * kChunkBytes, kChkDiscard, l, A.state_rows / 4))
+                if (ck<kCheck>(A, (l + 1) * 128 <= state_rows * kChunkBytes, kChkDiscard, l, state_rows / 4))
                     discard_l2(st + l * 128);
         }
 
         // --------------------------------------------------------------- Merge
-        if (ph.merge) {
+        if (merge) {
             uint32_t dj = 1;
             for (int j = 0; j < K; ++j) {
                 const uint32_t items = dj * (1u << (K - 1 - j)) * RE * 2;
@@ -532,11 +554,11 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             }
         }
 
-        if (!ph.reduce && !ph.chunk_mask && !ph.out) {
+        if (!reduce && !chunk_mask && !out) {
             // Merge only: write the rows the Merge created (rows whose group
             // digits are all 0/1 were read from the state unchanged), or all
             // rows when they came from the truth table.
-            const bool all = (ph.load == kLoadTT);
+            const bool all = (load == kLoadTT);
             for (uint32_t pc = tid; pc < R * 2; pc += kSThreads) {
                 const int h = pc & 1;
                 const uint32_t ri = pc >> 1;
@@ -545,8 +567,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 if (!all && !S.has_star[g]) continue;
                 const uint32_t e = ri - g * RE;
                 const uint64_t row = base + e + (uint64_t)g * w_g;
-                if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
-                A.state[2 * row + h] = tile[slot_s(ri, h)];
+                if (!ck<kCheck>(A, row < state_rows, kChkState, row, state_rows)) continue;
+                state[2 * row + h] = tile[slot_s(ri, h)];
             }
         } else {
             // ---------------------------------------------------------- Reduce
@@ -562,7 +584,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                     v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) acc[w] = 0;
-                    if (ph.reduce) {
+                    if (reduce) {
                         uint32_t gg = g, wgt = RE;
                         for (int j = 0; j < K; ++j) {
                             const uint32_t q = gg / 3u;
@@ -577,7 +599,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                             wgt *= 3;
                         }
                     }
-                    if (ph.chunk_mask) chunk_reduce_masked(v, acc, ph.chunk_mask);
+                    if (chunk_mask) chunk_reduce_masked(v, acc, chunk_mask);
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) res[rd][w] = v[w] & ~acc[w];
                 } else {
@@ -586,7 +608,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 }
             }
 
-            if (!ph.out) {
+            if (!out) {
                 __syncthreads();  // every read of the tile is done before rows are overwritten in place
 #pragma unroll
                 for (int rd = 0; rd < kRounds; ++rd) {
@@ -595,9 +617,9 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                         const uint32_t g = div_pow3(ri, B);
                         const uint32_t e = ri - g * RE;
                         const uint64_t row = base + e + (uint64_t)g * w_g;
-                        if (!ck<kCheck>(A, row < A.state_rows, kChkState, row, A.state_rows)) continue;
-                        A.state[2 * row] = make_uint4(res[rd][0], res[rd][1], res[rd][2], res[rd][3]);
-                        A.state[2 * row + 1] = make_uint4(res[rd][4], res[rd][5], res[rd][6], res[rd][7]);
+                        if (!ck<kCheck>(A, row < state_rows, kChkState, row, state_rows)) continue;
+                        state[2 * row] = make_uint4(res[rd][0], res[rd][1], res[rd][2], res[rd][3]);
+                        state[2 * row + 1] = make_uint4(res[rd][4], res[rd][5], res[rd][6], res[rd][7]);
                     }
                 }
             } else {
@@ -605,86 +627,36 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 // (B = 0, a = 0: rows base .. base + R - 1, contiguous.)
                 // Rows in rho order are (round, thread): per round, an
                 // inclusive warp scan of the row counts and the warp totals.
-                uint32_t rc[kRounds], incl[kRounds];
+                // excl[rd]: bits in this warp's rows before this thread's row
+                // of round rd (< 7776: 13 bits), row count in the top bits.
+                uint32_t cx[kRounds];
 #pragma unroll
                 for (int rd = 0; rd < kRounds; ++rd) {
                     uint32_t c = 0;
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) c += __popc(res[rd][w]);
-                    rc[rd] = c;
                     uint32_t x = c;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                         if (lane >= o) x += y;
                     }
-                    incl[rd] = x;
+                    cx[rd] = (c << 16) | (x - c);
                     if (lane == 31) S.warp_tot[rd][wid] = x;
                 }
                 __syncthreads();  // tile reads done; warp totals visible
-                uint32_t before[kRounds];
                 uint32_t tile_total = 0;
 #pragma unroll
-                for (int rd = 0; rd < kRounds; ++rd) {
-                    uint32_t rt = 0, bw = 0;
+                for (int rd = 0; rd < kRounds; ++rd)
 #pragma unroll
-                    for (int w = 0; w < kSThreads / 32; ++w) {
-                        const uint32_t v = S.warp_tot[rd][w];
-                        rt += v;
-                        if (w < wid) bw += v;
-                    }
-                    before[rd] = tile_total + bw + incl[rd] - rc[rd];
-                    tile_total += rt;
-                }
-                if (tid == 0 && tile_total) atomicAdd(A.count, (unsigned long long)tile_total);
-
-                if (A.pairs) {
-                    const uint64_t T = base / kTileRowsMax;
-                    if (wid == 0) {
-                        bool ok;
-                        const unsigned long long ex = lookback<kCheck>(A, T, tile_total, ok);
-                        if (lane == 0) {
-                            S.excl = ex;
-                            S.list_ok = ok;
-                            // mask / value bits of the digits above the tile (high digits >= 6)
-                            uint64_t x = T;
-                            uint32_t m = 0, v = 0;
-                            for (int d = 6; d < A.H; ++d) {
-                                const uint64_t q = x / 3u;
-                                const uint32_t dg = (uint32_t)(x - 3u * q);
-                                x = q;
-                                if (dg != 2) m |= 1u << (5 + d);
-                                if (dg == 1) v |= 1u << (5 + d);
-                            }
-                            S.tile_mask = m;
-                            S.tile_val = v;
-                        }
-                    }
-                    __syncthreads();
-                    if (S.list_ok) {
-                        const unsigned long long ex = S.excl;
-#pragma unroll
-                        for (int rd = 0; rd < kRounds; ++rd) {
-                            const uint32_t ri = rd * kSThreads + tid;
-                            unsigned long long k = ex + before[rd];
-                            if (rc[rd] && k < A.cap && ck<kCheck>(A, ri < (uint32_t)kTileRowsMax, kChkTable, ri, kTileRowsMax)) {
-                                const uint32_t rm = S.tile_mask | ((uint32_t)S.m6[ri] << 5);
-                                const uint32_t rv = S.tile_val | ((uint32_t)S.v6[ri] << 5);
-#pragma unroll
-                                for (int w = 0; w < kChunkWords; ++w) {
-                                    uint32_t bits = res[rd][w];
-                                    while (bits) {
-                                        const int b = __ffs(bits) - 1;
-                                        bits &= bits - 1;
-                                        const int q = 32 * w + b;  // < 243: padding bits stay 0
-                                        if (k < A.cap && q < 243)
-                                            A.pairs[k] = make_uint2((rm | S.t5m[q]) & A.nmask, (rv | S.t5v[q]) & A.nmask);
-                                        ++k;
-                                    }
-                                }
-                            }
-                        }
-                    }
+                    for (int w = 0; w < kSThreads / 32; ++w) tile_total += S.warp_tot[rd][w];
+                uint2 *const pairs = A.pairs;
+                const uint64_t T = base / kTileRowsMax;
+                if (tid == 0) {
+                    if (tile_total) atomicAdd(A.count, (unsigned long long)tile_total);
+                    // publish this tile's aggregate now; the prefix comes after the bitmap
+                    if (pairs && ck<kCheck>(A, T < A.out_tiles, kChkStatus, T, A.out_tiles))
+                        atomicExch(&A.status[T], (T == 0 ? kFlagP : kFlagA) | (unsigned long long)tile_total);
                 }
 
                 // Dense bitmap: rows base .. base+R-1 are bits base*243 ..
@@ -727,6 +699,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                     }
                 }
                 __syncthreads();
+                uint32_t *const outw = A.out;
+                const uint64_t alloc_words = A.out_alloc_words;
                 const bool last_tile = (base + R == A.total_rows);
                 const uint32_t tail = (o + L) & 31;
                 for (uint32_t cq = tid; cq < nq && cq < kSlots; cq += kSThreads) {
@@ -734,8 +708,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                     const long long i0 = (long long)(4 * cq) - (long long)sh;
                     if (i0 >= 1 && i0 + 3 <= (long long)nw - 2) {
                         const uint64_t wi = W0 + (uint64_t)i0;
-                        if (!ck<kCheck>(A, wi + 4 <= A.out_alloc_words, kChkOut, wi, A.out_alloc_words)) continue;
-                        *reinterpret_cast<uint4 *>(A.out + wi) = tile[cq];
+                        if (!ck<kCheck>(A, wi + 4 <= alloc_words, kChkOut, wi, alloc_words)) continue;
+                        *reinterpret_cast<uint4 *>(outw + wi) = tile[cq];
                         continue;
                     }
                     for (int x = 0; x < 4; ++x) {
@@ -745,8 +719,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                         const bool shared_prev = (i == 0 && o != 0);
                         const bool shared_next = (i == (long long)nw - 1 && !last_tile && tail != 0);
                         const uint64_t wi = W0 + (uint64_t)i;
-                        if (!ck<kCheck>(A, wi < A.out_alloc_words, kChkOut, wi, A.out_alloc_words)) continue;
-                        uint32_t *dst = A.out + wi;
+                        if (!ck<kCheck>(A, wi < alloc_words, kChkOut, wi, alloc_words)) continue;
+                        uint32_t *dst = outw + wi;
                         if (!shared_prev && !shared_next) {
                             *dst = val;
                         } else {
@@ -759,7 +733,69 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                     }
                 }
                 if (last_tile)
-                    for (uint64_t w = A.out_words + tid; w < A.out_alloc_words; w += kSThreads) A.out[w] = 0u;
+                    for (uint64_t w = A.out_words + tid; w < alloc_words; w += kSThreads) outw[w] = 0u;
+
+                if (pairs) {
+                    // The predecessors have had the bitmap's time to publish.
+                    if (wid == 0) {
+                        bool ok = true;
+                        unsigned long long ex = 0;
+                        if (T > 0) ex = lookback<kCheck>(A, T, tile_total, ok);
+                        if (lane == 0) {
+                            S.excl = ex;
+                            S.list_ok = ok;
+                            // mask / value bits of the digits above the tile (high digits >= 6)
+                            uint64_t x = T;
+                            uint32_t m = 0, v = 0;
+                            for (int d = 6; d < A.H; ++d) {
+                                const uint64_t q = x / 3u;
+                                const uint32_t dg = (uint32_t)(x - 3u * q);
+                                x = q;
+                                if (dg != 2) m |= 1u << (5 + d);
+                                if (dg == 1) v |= 1u << (5 + d);
+                            }
+                            S.tile_mask = m;
+                            S.tile_val = v;
+                        }
+                    }
+                    __syncthreads();
+                    if (S.list_ok) {
+                        const unsigned long long ex = S.excl;
+                        const uint64_t cap = A.cap;
+                        const uint32_t nmask = A.nmask;
+                        uint32_t round_base = 0;
+#pragma unroll
+                        for (int rd = 0; rd < kRounds; ++rd) {
+                            const uint32_t ri = rd * kSThreads + tid;
+                            uint32_t rt = 0, bw = 0;
+#pragma unroll
+                            for (int w = 0; w < kSThreads / 32; ++w) {
+                                const uint32_t v = S.warp_tot[rd][w];
+                                rt += v;
+                                if (w < wid) bw += v;
+                            }
+                            unsigned long long k = ex + round_base + bw + (cx[rd] & 0xffffu);
+                            round_base += rt;
+                            if ((cx[rd] >> 16) && k < cap &&
+                                ck<kCheck>(A, ri < (uint32_t)kTileRowsMax, kChkTable, ri, kTileRowsMax)) {
+                                const uint32_t rm = S.tile_mask | ((uint32_t)S.m6[ri] << 5);
+                                const uint32_t rv = S.tile_val | ((uint32_t)S.v6[ri] << 5);
+#pragma unroll
+                                for (int w = 0; w < kChunkWords; ++w) {
+                                    uint32_t bits = res[rd][w];
+                                    while (bits) {
+                                        const int b = __ffs(bits) - 1;
+                                        bits &= bits - 1;
+                                        const int q = 32 * w + b;  // < 243: padding bits stay 0
+                                        if (k < cap && q < 243)
+                                            pairs[k] = make_uint2((rm | S.t5m[q]) & nmask, (rv | S.t5v[q]) & nmask);
+                                        ++k;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
             }
         }
 
@@ -768,8 +804,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
-                const uint64_t di = sp.done_off + sb * sp.nph + p;
-                if (ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words)) atomicAdd(done + sb * sp.nph + p, 1u);
+                const uint64_t di = sp.done_off + sb * nph + p;
+                if (ck<kCheck>(A, di < A.ctrl_words, kChkCtrl, di, A.ctrl_words)) atomicAdd(done + sb * nph + p, 1u);
             }
         }
         __syncthreads();  // the shared tile and S are reused by the next ticket

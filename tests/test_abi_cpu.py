@@ -210,38 +210,28 @@ def test_plan_rows_in_bounds(n):
 
 # ------------------------------------------------- ticket order (host replica)
 
-def step_offset(sp, k):
-    off = 0
-    for p_, ph in enumerate(sp["phases"]):
-        if k <= p_:
-            continue
-        off += min((k - p_) * sp["window"], sp["n_sb"]) * ph["tiles"]
-    return off
-
-
 def decode_ticket(sp, ticket):
-    nph = len(sp["phases"])
-    groups = -(-sp["n_sb"] // sp["window"])
-    lo, hi = 0, groups + nph - 1
-    while hi - lo > 1:
-        mid = (lo + hi) // 2
-        if step_offset(sp, mid) <= ticket:
-            lo = mid
-        else:
-            hi = mid
-    rem = ticket - step_offset(sp, lo)
-    for p_, ph in enumerate(sp["phases"]):
-        if lo < p_:
-            break
-        g = lo - p_
-        if g >= groups:
-            continue
-        nsb = min(sp["window"], sp["n_sb"] - g * sp["window"])
-        cnt = nsb * ph["tiles"]
-        if rem < cnt:
-            return p_, g * sp["window"] + rem // ph["tiles"], rem % ph["tiles"]
-        rem -= cnt
-    raise AssertionError("ticket out of range")
+    """Replica of the device decode: fixed-size pipeline steps; None = empty ticket."""
+    step, r = divmod(ticket, sp["step_size"])
+    offs, acc = [], 0
+    for ph in sp["phases"]:
+        offs.append(acc)
+        acc += sp["window"] * ph["tiles"]
+    p_ = len(sp["phases"]) - 1
+    while p_ > 0 and r < offs[p_]:
+        p_ -= 1
+    r -= offs[p_]
+    if step < p_:
+        return None
+    g = step - p_
+    if g >= sp["groups"]:
+        return None
+    tiles = sp["phases"][p_]["tiles"]
+    sbl, t = divmod(r, tiles)
+    sb = g * sp["window"] + sbl
+    if sb >= sp["n_sb"]:
+        return None
+    return p_, sb, t
 
 
 @pytest.mark.parametrize("n", [13, 15, 16, 18, 21, 24])
@@ -253,20 +243,28 @@ def test_ticket_order_is_a_valid_schedule(n):
     for sp in p["passes"]:
         if sp["kind"] == "whole":
             continue
-        total = sum(ph["tiles"] for ph in sp["phases"]) * sp["n_sb"]
-        budget = 400000
-        if total > budget:
+        want = sum(ph["tiles"] for ph in sp["phases"]) * sp["n_sb"]
+        assert sp["step_size"] == sp["window"] * sum(ph["tiles"] for ph in sp["phases"])
+        assert sp["n_steps"] == sp["groups"] + len(sp["phases"]) - 1
+        assert sp["groups"] == -(-sp["n_sb"] // sp["window"])
+        if want > 400000:
             # large plans: same window, truncated to a few super-block groups
-            sp = dict(sp, n_sb=min(sp["n_sb"], 7 * sp["window"] + 3))
-            total = sum(ph["tiles"] for ph in sp["phases"]) * sp["n_sb"]
+            nsb = min(sp["n_sb"], 7 * sp["window"] + 3)
+            sp = dict(sp, n_sb=nsb, groups=-(-nsb // sp["window"]))
+            sp["n_steps"] = sp["groups"] + len(sp["phases"]) - 1
+            want = sum(ph["tiles"] for ph in sp["phases"]) * sp["n_sb"]
+        total = sp["n_steps"] * sp["step_size"]
+        assert total < 2 ** 32
         seen = {}
         last_of = {}
         for tk in range(total):
             key = decode_ticket(sp, tk)
+            if key is None:
+                continue
             assert key not in seen
             seen[key] = tk
             last_of[(key[0], key[1])] = max(last_of.get((key[0], key[1]), -1), tk)
-        assert len(seen) == total
+        assert len(seen) == want
         for (ph, sb, t), tk in seen.items():
             if ph > 0:
                 assert last_of[(ph - 1, sb)] < tk
