@@ -225,7 +225,8 @@ CtrlLayout ctrl_layout(const Plan &p)
     CtrlLayout c;
     const uint64_t u32 = 1 + kCtrlTickets + p.n_done;
     c.status_u64 = (u32 * 4 + 7) / 8;
-    c.bytes = align_up((c.status_u64 + p.out_tiles) * 8, 256);
+    c.timing_off = (c.status_u64 + p.out_tiles) * 8;
+    c.bytes = align_up(c.timing_off + 8 * kTimingWordsPerPass * 4, 256);
     return c;
 }
 
@@ -509,6 +510,22 @@ extern "C" int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const
     int st = sweep_dev(n, pass, pass + 1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream);
     if (st || !d_pairs || pass != plan_passes(plan) - 1) return st;
     return dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
+}
+
+extern "C" int dqmc_debug_timing(uint32_t n, const void *d_work, uint64_t work_bytes, uint64_t *out,
+                                 uint64_t out_words, void *stream)
+{
+    if (n > DQMC_MAX_N || !d_work || !out) return DQMC_EINVAL;
+    const Plan plan = make_plan((int)n);
+    const Workspace w = workspace_layout((int)n);
+    if (plan.sps.empty() || work_bytes < w.total) return DQMC_EINVAL;
+    const CtrlLayout cl = ctrl_layout(plan);
+    const uint64_t words = std::min<uint64_t>(out_words, (uint64_t)kTimingWordsPerPass * 4);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, static_cast<const char *>(d_work) + w.ctrl_off + cl.timing_off, 8 * words,
+                       cudaMemcpyDeviceToHost);
+    return map_cuda(e);
 }
 
 extern "C" int dqmc_selftest_timeout(uint32_t n, void *d_work, uint64_t work_bytes, uint64_t wait_ns, void *stream)

@@ -134,8 +134,10 @@ struct CtrlLayout {
     uint64_t tickets = 1;       // uint32 index
     uint64_t done = 1 + kCtrlTickets;
     uint64_t status_u64 = 0;    // uint64 index from ctrl base
+    uint64_t timing_off = 0;    // bytes: per pass 3 phases x 8 segment cycle sums (uint64)
     uint64_t bytes = 0;
 };
+constexpr int kTimingWordsPerPass = 3 * 8;
 CtrlLayout ctrl_layout(const Plan &p);
 
 // Status word written by a timed-out device wait (dqmc_dev_status reads it).

@@ -78,6 +78,7 @@ struct SweepArgs {
     // buffer sizes for the bounds checks
     uint64_t state_rows, tt_words, out_tiles, ctrl_words;
     int l2_discard;             // drop dead state lines from L2 in the bitmap phase
+    unsigned long long *timing; // per-phase cycle sums of the tile segments (null: off)
 };
 
 // Bounds checks: every global and shared index is compared with its buffer
@@ -101,6 +102,7 @@ __device__ __forceinline__ bool ck(const SweepArgs &A, bool cond, int what, uint
 }
 
 constexpr int kSThreads = 256;
+constexpr int kTimeSegs = 8;  // ticket+wait, load, merge, reduce, store/out, signal, tiles, (spare)
 constexpr int kRounds = (kTileRowsMax + kSThreads - 1) / kSThreads;  // 3
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -318,6 +320,7 @@ struct TileShared {
     unsigned long long excl;        // primes in the bitmap tiles before this one
     uint32_t tile_mask, tile_val;   // mask / value bits of the digits above the bitmap tile
     int p, abort, stop, list_ok;
+    unsigned long long tsum[kMaxPhases][8];  // timing sums (thread 0)
 };
 
 // Mixed-radix decode of x over a list of fixed digits (first entry least
@@ -426,6 +429,22 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
     // Thread 0 holds the next ticket: it is taken while the current tile runs.
     uint32_t next = 0xffffffffu;
     if (tid == 0 && slot_ok) next = atomicAdd(tickets + slot, 1u);
+    // Optional timing (thread 0): cycles per tile segment, summed per phase.
+    const bool timing = (A.timing != nullptr);
+    unsigned long long(&tsum)[kMaxPhases][kTimeSegs] = S.tsum;
+    if (tid == 0)
+        for (int q = 0; q < kMaxPhases; ++q)
+            for (int g = 0; g < kTimeSegs; ++g) tsum[q][g] = 0;
+    unsigned long long tcur = timing ? clock64() : 0ull;
+    int tph = 0;
+#define DQMC_TSEG(seg)                                                       \
+    do {                                                                     \
+        if (timing && tid == 0) {                                            \
+            const unsigned long long now_ = clock64();                       \
+            tsum[tph][(seg)] += now_ - tcur;                                 \
+            tcur = now_;                                                     \
+        }                                                                    \
+    } while (0)
 
     for (;;) {
         if (tid == 0) {
@@ -462,6 +481,8 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
         __syncthreads();
         if (S.stop) break;
         const int p = S.p;
+        tph = p;
+        DQMC_TSEG(0);  // ticket, decode, dependency wait
         const uint64_t sb = S.sb;
         const uint64_t base = S.base, ttb = S.ttb;
         const bool signal = (p < nph - 1);   // later phases of this block wait for this tile
@@ -517,6 +538,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             asm volatile("cp.async.wait_all;\n" ::: "memory");
         }
         __syncthreads();
+        DQMC_TSEG(1);  // load
         if (out && A.l2_discard) {
             // The bitmap phase is the last reader of these rows: drop their
             // lines from L2 without writing them back (off unless
@@ -554,6 +576,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             }
         }
 
+        DQMC_TSEG(2);  // Merge
         if (!reduce && !chunk_mask && !out) {
             // Merge only: write the rows the Merge created (rows whose group
             // digits are all 0/1 were read from the state unchanged), or all
@@ -608,6 +631,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
                 }
             }
 
+            DQMC_TSEG(3);  // Reduce (this thread)
             if (!out) {
                 __syncthreads();  // every read of the tile is done before rows are overwritten in place
 #pragma unroll
@@ -799,6 +823,7 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             }
         }
 
+        DQMC_TSEG(4);  // store / bitmap / list
         // ------------------------------------------------------------- signal
         if (signal) {
             __syncthreads();
@@ -809,7 +834,14 @@ super_pass_kernel(const __grid_constant__ SuperPassDesc sp_param, const __grid_c
             }
         }
         __syncthreads();  // the shared tile and S are reused by the next ticket
+        DQMC_TSEG(5);  // signal, end barrier
+        if (timing && tid == 0) tsum[tph][6] += 1;  // tiles
     }
+#undef DQMC_TSEG
+    if (timing && tid == 0)
+        for (int q = 0; q < kMaxPhases; ++q)
+            for (int g = 0; g < kTimeSegs; ++g)
+                if (tsum[q][g]) atomicAdd(A.timing + q * kTimeSegs + g, tsum[q][g]);
 }
 
 // One thread waits on a phase counter that nothing increments: the bounded
@@ -886,9 +918,17 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
     a.out_tiles = plan.out_tiles;
     a.ctrl_words = cl.bytes / 4;
     a.l2_discard = discard ? 1 : 0;
+    static const bool timing_on = [] {
+        const char *v = getenv("DQMC_TIMING");
+        return v && v[0] == '1';
+    }();
+    a.timing = timing_on ? reinterpret_cast<unsigned long long *>(static_cast<char *>(d_ctrl) + cl.timing_off)
+                         : nullptr;
     const int resident = occupancy_blocks(smem);
+    unsigned long long *const timing0 = a.timing;
     for (int i = first; i < last; ++i) {
         const SuperPassDesc &sp = plan.sps[i];
+        a.timing = timing0 ? timing0 + (size_t)i * kTimingWordsPerPass : nullptr;
         uint64_t tickets = 0;
         for (int p = 0; p < sp.nph; ++p) tickets += (uint64_t)sp.ph[p].tiles * sp.n_sb;
         const uint64_t grid = tickets < (uint64_t)resident ? tickets : (uint64_t)resident;

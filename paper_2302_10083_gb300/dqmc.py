@@ -62,6 +62,7 @@ _SIGS = {
     "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
                                            ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
+    "dqmc_debug_timing": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_vp]),
 }
 
 
@@ -208,6 +209,13 @@ def dqmc_list_dev(n, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_b
 
 def dqmc_dev_status(n, d_work, work_bytes, stream) -> int:
     return _check(lib().dqmc_dev_status(n, d_work, work_bytes, stream or None), "dqmc_dev_status")
+
+
+def dqmc_debug_timing(n, d_work, work_bytes, stream, passes=4):
+    """Per-pass, per-phase cycle sums of the super-pass tile segments (DQMC_TIMING=1)."""
+    out = (ctypes.c_uint64 * (24 * passes))()
+    _check(lib().dqmc_debug_timing(n, d_work, work_bytes, out, 24 * passes, stream or None), "dqmc_debug_timing")
+    return np.array(out, dtype=np.uint64).reshape(passes, 3, 8)
 
 
 def dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:
