@@ -137,6 +137,23 @@ int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc,
  * spin unbounded. */
 int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *stream);
 
+/* For callers that cannot allocate device memory (an application whose own
+ * pool owns the device memory, or code on a latency path where an allocation,
+ * which may synchronise the device, is not acceptable).  Same result as
+ * dqmc_primes_dev, without a workspace argument: the workspace is a static
+ * device array of 2 MiB inside the library (held by every GPU that loads the
+ * library until the process exits), so only n <= 15 is accepted; larger n
+ * returns DQMC_EINVAL.  Nothing is allocated: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each sweep clears
+ * what must start at zero); calls that overlap on the GPU, on any stream or
+ * thread, race on it and must be serialised by the caller.  d_on, d_dc,
+ * d_bitmap, d_count and stream as for dqmc_primes_dev.  The paper has no
+ * counterpart: this is a deployment convenience. */
+int dqmc_primes_dev_static(uint32_t n, const void *d_on, const void *d_dc,
+                           void *d_bitmap, uint64_t *d_count, void *stream);
+
 /* Compaction alone: (mask, value) pairs of the set bits of an existing dense
  * bitmap of an n-variable function.  d_work as above (only its scan part is
  * used).  d_count: one uint64 (required). */

@@ -62,6 +62,7 @@ _SIGS = {
     "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
                                            ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
+    "dqmc_primes_dev_static": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dqmc_debug_timing": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_vp]),
 }
 
@@ -209,6 +210,12 @@ def dqmc_list_dev(n, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_b
 
 def dqmc_dev_status(n, d_work, work_bytes, stream) -> int:
     return _check(lib().dqmc_dev_status(n, d_work, work_bytes, stream or None), "dqmc_dev_status")
+
+
+def dqmc_primes_dev_static(n, d_on, d_dc, d_bitmap, d_count, stream) -> int:
+    """dqmc_primes_dev with the library's static 2 MiB workspace (n <= 15, allocates nothing)."""
+    return _check(lib().dqmc_primes_dev_static(n, d_on, d_dc or None, d_bitmap, d_count or None, stream or None),
+                  "dqmc_primes_dev_static")
 
 
 def dqmc_debug_timing(n, d_work, work_bytes, stream, passes=4):
