@@ -58,17 +58,6 @@ int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const void *d_dc
 int dqmc_selftest_timeout(uint32_t n, void *d_work, uint64_t work_bytes,
                           uint64_t wait_ns, void *stream);
 
-/* Diagnostics: when the environment variable DQMC_TIMING=1 is set before the
- * first sweep, the super-pass kernels of n >= 13 sum, per phase, the SM cycles
- * that thread 0 of each CTA spends in each tile segment.  This call waits for
- * `stream` and copies those sums (uint64, [pass][phase 0..2][segment 0..7]:
- * ticket + dependency wait, load, Merge, Reduce, store / bitmap / list,
- * signal, tile count, spare) of the last sweep on d_work into out (at most
- * out_words words).  Zero when timing is off.  The paper has no counterpart:
- * this is a measurement aid. */
-int dqmc_debug_timing(uint32_t n, const void *d_work, uint64_t work_bytes, uint64_t *out,
-                      uint64_t out_words, void *stream);
-
 #ifdef __cplusplus
 }
 #endif

@@ -24,21 +24,19 @@ uint64_t bitmap_alloc_bytes(int n) { return align_up((pow3(n) + 7) / 8, 16); }
 // n <= 12: one tile holds the whole function in shared memory (one pass of
 // the tile_pass kernel in dqmc_sweep.cu).
 //
-// n >= 13 (H = n - 5 >= 8 high digits), persistent super-passes
-// (dqmc_super.cu):
-//   1 first   truth table -> Merge chunk digits and high digits 0..5; rows with
-//             the digits >= 6 still 0/1;
-//   2 merge   Merge digits 6..9 (only when H > 10), sparse rows in and out;
-//   3 A       Merge digits 10..H-1 and Reduce them together with the five chunk
-//             digits (H <= 10: digits 6..H-1).  When there are more than five
-//             such digits they are split in two groups GA < GB and the
-//             super-block (inner digits + GA + GB) runs three phases: Merge GA,
-//             Merge + Reduce GB, Reduce GA.  This pass writes the whole state.
-//   4 B       Reduce digits 6..9 (phase a) and 0..5 (phase b, which writes the
-//             dense bitmap, the count and the list) on super-blocks of digits
-//             0..9 (H <= 10: phase b only).
-// Every digit is merged once before any Reduce and reduced exactly once; the
-// chunk digits in pass A.
+// n >= 13 (H = n - 5 >= 8 high digits): streaming passes of 2187-row tiles
+// (dqmc_pass.cu).  The high digits are split into a first group G0 = 0..6 and
+// groups G1 < G2 < ... of at most 6 digits; a tile holds one group's digits
+// plus 7 - K inner digits (the lowest high digits) for contiguous runs.
+//   first       truth table -> Merge chunk digits and G0 (digits >= 7 still 0/1)
+//   merge       Merge G1 .. G(last-1), sparse rows in and out
+//   merge-last  Merge the last group, then Reduce it and chunk digits {0, 1}
+//               (all of {0, 1, 2} when there is no middle group)
+//   reduce      Reduce the middle groups, top down; the first of them also
+//               Reduces chunk digits {2, 3, 4}
+//   out         Reduce G0 (and chunk digits {3, 4} when there is no middle
+//               group), write the dense bitmap, the count and the list.
+// Every digit is merged once before any Reduce and reduced exactly once.
 
 static FixedDigits fixed_of(const std::vector<int> &digits, const std::vector<bool> &merged)
 {
@@ -60,56 +58,30 @@ static uint64_t radix_product(const FixedDigits &f)
     return t;
 }
 
-// A phase over group digits a..a+K-1 with inner digits 0..B-1 inside a
-// super-block whose digit set is sb_digits; the other super-block digits are
-// fixed per tile.
-static PhaseDesc make_phase(int load, int a, int K, int B, const std::vector<int> &sb_digits,
-                            const std::vector<bool> &merged)
+// One pass = one phase over tiles of group digits a..a+K-1 and inner digits
+// 0..B-1; every other high digit is fixed per tile (radix 2 while it is not
+// merged yet, else 3), in ascending digit order, so tile index order is rho
+// order.
+static SuperPassDesc make_pass(int load, int a, int K, int B, int H, const std::vector<bool> &merged)
 {
-    PhaseDesc ph;
+    SuperPassDesc sp;
+    sp.nph = 1;
+    PhaseDesc &ph = sp.ph[0];
     ph.load = load;
     ph.a = a;
     ph.K = K;
     ph.B = B;
-    std::vector<int> fixed;
-    for (int d : sb_digits)
-        if (d >= B && !(d >= a && d < a + K)) fixed.push_back(d);
-    ph.fix = fixed_of(fixed, merged);
-    ph.tiles = (uint32_t)radix_product(ph.fix);
-    return ph;
-}
-
-static void finish_superpass(SuperPassDesc &sp, const std::vector<int> &sb_digits, int H,
-                             const std::vector<bool> &merged_before, uint32_t window)
-{
+    ph.tiles = 1;
     std::vector<int> outer;
     for (int d = 0; d < H; ++d)
-        if (std::find(sb_digits.begin(), sb_digits.end(), d) == sb_digits.end()) outer.push_back(d);
-    sp.sb = fixed_of(outer, merged_before);
+        if (!(d < B) && !(d >= a && d < a + K)) outer.push_back(d);
+    sp.sb = fixed_of(outer, merged);
     sp.n_sb = radix_product(sp.sb);
-    sp.window = window ? window : (uint32_t)std::min<uint64_t>(sp.n_sb, 0xffffffffu);
-    sp.groups = (uint32_t)((sp.n_sb + sp.window - 1) / sp.window);
-    uint32_t off = 0;
-    for (int p = 0; p < sp.nph; ++p) {
-        sp.ph_off[p] = off;
-        off += sp.window * sp.ph[p].tiles;
-    }
-    sp.step_size = off;
-    sp.n_steps = sp.groups + sp.nph - 1;
-}
-
-static std::vector<int> range_digits(int lo, int hi)
-{
-    std::vector<int> v;
-    for (int d = lo; d < hi; ++d) v.push_back(d);
-    return v;
-}
-
-static std::vector<int> concat(std::vector<int> a, const std::vector<int> &b)
-{
-    a.insert(a.end(), b.begin(), b.end());
-    std::sort(a.begin(), a.end());
-    return a;
+    sp.window = (uint32_t)std::min<uint64_t>(sp.n_sb, 0xffffffffu);
+    sp.groups = 1;
+    sp.step_size = (uint32_t)sp.n_sb;
+    sp.n_steps = 1;
+    return sp;
 }
 
 Plan make_plan(int n)
@@ -130,93 +102,55 @@ Plan make_plan(int n)
         return p;
     }
     p.state_rows = pow3(H);
+    std::vector<int> starts, sizes;
+    const int rest = H - kTileDigits;
+    const int ng = (rest + kMaxStreamGroup - 1) / kMaxStreamGroup;
+    int at = kTileDigits;
+    for (int i = 0; i < ng; ++i) {
+        const int k = rest / ng + (i < rest % ng ? 1 : 0);
+        starts.push_back(at);
+        sizes.push_back(k);
+        at += k;
+    }
     std::vector<bool> merged(H, false);
     int slot = 0;
-
-    {   // 1: first -- digits 0..5 from the truth table
-        SuperPassDesc sp;
-        sp.nph = 1;
-        const std::vector<int> sbd = range_digits(0, 6);
-        sp.ph[0] = make_phase(kLoadTT, 0, 6, 0, sbd, merged);
+    auto push = [&](SuperPassDesc sp) {
+        sp.slot = slot++;
+        p.sps.push_back(sp);
+    };
+    {   // first: G0 from the truth table
+        SuperPassDesc sp = make_pass(kLoadTT, 0, kTileDigits, 0, H, merged);
         sp.ph[0].merge = 1;
-        finish_superpass(sp, sbd, H, merged, 0);
-        sp.slot = slot++;
-        p.sps.push_back(sp);
-        for (int d = 0; d < 6; ++d) merged[d] = true;
+        push(sp);
+        for (int d = 0; d < kTileDigits; ++d) merged[d] = true;
     }
-    const int top0 = H > 10 ? 10 : 6;  // first digit of pass A
-    if (H > 10) {   // 2: merge -- digits 6..9
-        SuperPassDesc sp;
-        sp.nph = 1;
-        const std::vector<int> sbd = concat(range_digits(0, 2), range_digits(6, 10));
-        sp.ph[0] = make_phase(kLoadSparse, 6, 4, 2, sbd, merged);
+    for (int i = 0; i < ng; ++i) {   // merge G1 .. ; the last one also Reduces
+        const int a = starts[i], K = sizes[i], B = kTileDigits - K;
+        SuperPassDesc sp = make_pass(kLoadSparse, a, K, B, H, merged);
         sp.ph[0].merge = 1;
-        finish_superpass(sp, sbd, H, merged, 0);
-        sp.slot = slot++;
-        p.sps.push_back(sp);
-        for (int d = 6; d < 10; ++d) merged[d] = true;
-    }
-    {   // 3: A -- Merge and Reduce digits top0..H-1, Reduce the chunk digits
-        const int m = H - top0;
-        SuperPassDesc sp;
-        if (m <= 5) {
-            const int B = 6 - m;
-            const std::vector<int> sbd = concat(range_digits(0, B), range_digits(top0, H));
-            sp.nph = 1;
-            sp.ph[0] = make_phase(kLoadSparse, top0, m, B, sbd, merged);
-            sp.ph[0].merge = sp.ph[0].reduce = 1;
-            sp.ph[0].chunk_mask = 31;
-            finish_superpass(sp, sbd, H, merged, 0);
-        } else {
-            const int m1 = m / 2, m2 = m - m1;   // m1 <= m2 <= 5
-            const int Ba = 6 - m1, Bb = 6 - m2;
-            const std::vector<int> sbd = concat(range_digits(0, Ba), range_digits(top0, H));
-            std::vector<bool> mg = merged;
-            sp.nph = 3;
-            sp.ph[0] = make_phase(kLoadSparse, top0, m1, Ba, sbd, mg);       // Merge GA
-            sp.ph[0].merge = 1;
-            for (int d = top0; d < top0 + m1; ++d) mg[d] = true;
-            sp.ph[1] = make_phase(kLoadSparse, top0 + m1, m2, Bb, sbd, mg);  // Merge + Reduce GB
-            sp.ph[1].merge = sp.ph[1].reduce = 1;
-            sp.ph[1].chunk_mask = 31;
-            for (int d = top0 + m1; d < H; ++d) mg[d] = true;
-            sp.ph[2] = make_phase(kLoadFull, top0, m1, Ba, sbd, mg);         // Reduce GA
-            sp.ph[2].reduce = 1;
-            finish_superpass(sp, sbd, H, merged, 2);
-        }
-        sp.slot = slot++;
-        p.sps.push_back(sp);
-        for (int d = top0; d < H; ++d) merged[d] = true;
-    }
-    {   // 4: B -- Reduce digits 6..9 (when pass A did not) and 0..5, write the bitmap
-        SuperPassDesc sp;
-        if (top0 == 10) {
-            const std::vector<int> sbd = range_digits(0, 10);
-            sp.nph = 2;
-            sp.ph[0] = make_phase(kLoadFull, 6, 4, 2, sbd, merged);
+        if (i == ng - 1) {
             sp.ph[0].reduce = 1;
-            sp.ph[1] = make_phase(kLoadFull, 0, 6, 0, sbd, merged);
-            sp.ph[1].reduce = 1;
-            sp.ph[1].out = 1;
-            finish_superpass(sp, sbd, H, merged, 6);
-        } else {
-            const std::vector<int> sbd = range_digits(0, 6);
-            sp.nph = 1;
-            sp.ph[0] = make_phase(kLoadFull, 0, 6, 0, sbd, merged);
-            sp.ph[0].reduce = 1;
-            sp.ph[0].out = 1;
-            finish_superpass(sp, sbd, H, merged, 0);
+            sp.ph[0].chunk_mask = (ng >= 2) ? 0x03 : 0x07;
         }
-        sp.slot = slot++;
-        p.sps.push_back(sp);
+        push(sp);
+        for (int d = a; d < a + K; ++d) merged[d] = true;
     }
-    uint64_t done = 1 + kCtrlTickets;
-    for (auto &sp : p.sps) {
-        sp.done_off = done;
-        done += sp.n_sb * sp.nph;
+    for (int i = ng - 2; i >= 0; --i) {   // reduce the middle groups, top down
+        const int a = starts[i], K = sizes[i], B = kTileDigits - K;
+        SuperPassDesc sp = make_pass(kLoadFull, a, K, B, H, merged);
+        sp.ph[0].reduce = 1;
+        sp.ph[0].chunk_mask = (i == ng - 2) ? 0x1c : 0;
+        push(sp);
     }
-    p.n_done = done - (1 + kCtrlTickets);
-    p.out_tiles = pow3(H) / kTileRowsMax;
+    {   // out: G0, the bitmap, the count and the list
+        SuperPassDesc sp = make_pass(kLoadFull, 0, kTileDigits, 0, H, merged);
+        sp.ph[0].reduce = 1;
+        sp.ph[0].out = 1;
+        sp.ph[0].chunk_mask = (ng >= 2) ? 0 : 0x18;
+        push(sp);
+    }
+    p.n_done = 0;
+    p.out_tiles = pow3(H) / kTileRows;
     return p;
 }
 
@@ -225,8 +159,7 @@ CtrlLayout ctrl_layout(const Plan &p)
     CtrlLayout c;
     const uint64_t u32 = 1 + kCtrlTickets + p.n_done;
     c.status_u64 = (u32 * 4 + 7) / 8;
-    c.timing_off = (c.status_u64 + p.out_tiles) * 8;
-    c.bytes = align_up(c.timing_off + 8 * kTimingWordsPerPass * 4, 256);
+    c.bytes = align_up((c.status_u64 + p.out_tiles) * 8, 256);
     return c;
 }
 
@@ -510,22 +443,6 @@ extern "C" int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const
     int st = sweep_dev(n, pass, pass + 1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream);
     if (st || !d_pairs || pass != plan_passes(plan) - 1) return st;
     return dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
-}
-
-extern "C" int dqmc_debug_timing(uint32_t n, const void *d_work, uint64_t work_bytes, uint64_t *out,
-                                 uint64_t out_words, void *stream)
-{
-    if (n > DQMC_MAX_N || !d_work || !out) return DQMC_EINVAL;
-    const Plan plan = make_plan((int)n);
-    const Workspace w = workspace_layout((int)n);
-    if (plan.sps.empty() || work_bytes < w.total) return DQMC_EINVAL;
-    const CtrlLayout cl = ctrl_layout(plan);
-    const uint64_t words = std::min<uint64_t>(out_words, (uint64_t)kTimingWordsPerPass * 4);
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(out, static_cast<const char *>(d_work) + w.ctrl_off + cl.timing_off, 8 * words,
-                       cudaMemcpyDeviceToHost);
-    return map_cuda(e);
 }
 
 extern "C" int dqmc_selftest_timeout(uint32_t n, void *d_work, uint64_t work_bytes, uint64_t wait_ns, void *stream)

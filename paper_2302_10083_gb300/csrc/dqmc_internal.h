@@ -45,7 +45,6 @@ struct Pass {
 // stay in L2 between phases.
 constexpr int kMaxPhases = 3;
 constexpr int kMaxFixed = 24;
-constexpr int kTileRowsMax = 729;   // 3^6 rows x 32 bytes = 23 KB of shared memory
 
 enum LoadKind : int { kLoadTT = 0, kLoadSparse = 1, kLoadFull = 2 };
 
@@ -96,7 +95,9 @@ struct Plan {
 };
 
 constexpr int kMaxSmemGroup = 7;    // 3^7 rows x 32 B = 70 KB of shared memory
-constexpr int kMaxStreamGroup = 6;  // with one inner digit: 3^6 x 3 rows
+constexpr int kMaxStreamGroup = 6;  // digits of a group after the first
+constexpr int kTileDigits = 7;      // group + inner digits of a streaming tile
+constexpr int kTileRows = 2187;     // 3^7
 
 Plan make_plan(int n);
 std::string describe_plan(const Plan &p);
@@ -134,10 +135,8 @@ struct CtrlLayout {
     uint64_t tickets = 1;       // uint32 index
     uint64_t done = 1 + kCtrlTickets;
     uint64_t status_u64 = 0;    // uint64 index from ctrl base
-    uint64_t timing_off = 0;    // bytes: per pass 3 phases x 8 segment cycle sums (uint64)
     uint64_t bytes = 0;
 };
-constexpr int kTimingWordsPerPass = 3 * 8;
 CtrlLayout ctrl_layout(const Plan &p);
 
 // Status word written by a timed-out device wait (dqmc_dev_status reads it).
@@ -145,7 +144,8 @@ constexpr uint32_t kErrTimeout = 0x54494d45u;  // "TIME"
 // Status word of the checked build when an index fell outside its buffer.
 constexpr uint32_t kErrBounds = 0x424f554eu;   // "BOUN"
 
-// Enqueue the super-passes of a plan (n >= 13).  d_pairs may be null (no list).
+// Enqueue passes [first, last) of a plan (n >= 13, dqmc_pass.cu).  d_pairs
+// may be null (no list).
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
                          uint32_t *d_bitmap, unsigned long long *d_count, uint32_t *d_pairs,
                          uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last);

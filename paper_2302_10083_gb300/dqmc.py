@@ -63,7 +63,6 @@ _SIGS = {
                                            ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
     "dqmc_primes_dev_static": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp]),
-    "dqmc_debug_timing": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_vp]),
 }
 
 
@@ -216,13 +215,6 @@ def dqmc_primes_dev_static(n, d_on, d_dc, d_bitmap, d_count, stream) -> int:
     """dqmc_primes_dev with the library's static 2 MiB workspace (n <= 15, allocates nothing)."""
     return _check(lib().dqmc_primes_dev_static(n, d_on, d_dc or None, d_bitmap, d_count or None, stream or None),
                   "dqmc_primes_dev_static")
-
-
-def dqmc_debug_timing(n, d_work, work_bytes, stream, passes=4):
-    """Per-pass, per-phase cycle sums of the super-pass tile segments (DQMC_TIMING=1)."""
-    out = (ctypes.c_uint64 * (24 * passes))()
-    _check(lib().dqmc_debug_timing(n, d_work, work_bytes, out, 24 * passes, stream or None), "dqmc_debug_timing")
-    return np.array(out, dtype=np.uint64).reshape(passes, 3, 8)
 
 
 def dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:

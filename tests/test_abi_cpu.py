@@ -120,7 +120,7 @@ def test_plan_digit_coverage(n):
     for sp in p["passes"]:
         for ph in sp["phases"]:
             digits = list(range(ph["a"], ph["a"] + ph["K"]))
-            assert ph["K"] + ph["B"] <= (7 if sp["kind"] == "whole" else 6)
+            assert ph["K"] + ph["B"] <= 7
             assert ph["B"] <= ph["a"] or ph["K"] == 0 or ph["a"] == 0
             if ph["merge"]:
                 assert not merge_done or ph["reduce"], "a Merge after the first Reduce"
@@ -139,8 +139,11 @@ def test_plan_digit_coverage(n):
     assert sum(outs) == 1
     if H > 7:
         assert p["state_rows"] == 3 ** H
-        assert last["a"] == 0 and last["B"] == 0 and last["K"] == 6
-        assert p["out_tiles"] == 3 ** H // 729
+        assert last["a"] == 0 and last["B"] == 0 and last["K"] == 7
+        assert p["out_tiles"] == 3 ** H // 2187
+        for sp in p["passes"]:
+            ph = sp["phases"][0]
+            assert ph["K"] + ph["B"] == 7   # 2187-row tiles
 
 
 @pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
@@ -197,14 +200,14 @@ def test_plan_rows_in_bounds(n):
             top = last_sb + decode_fixed(ph["fix"], ph["tiles"] - 1)
             row_max = top + 3 ** ph["B"] - 1 + (3 ** ph["K"] - 1) * 3 ** ph["a"]
             assert row_max < 3 ** H
-            assert 3 ** (ph["K"] + ph["B"]) <= 729
+            assert 3 ** (ph["K"] + ph["B"]) <= 2187
             tickets += ph["tiles"] * sp["n_sb"]
             if ph["load"] == "tt":
                 # truth-table words: binary value of the fixed digits times 2^K + gb < 2^H
                 tt = sum(2 ** d for d, r in sp["sb"]) + 2 ** ph["K"] - 1
                 assert tt < 2 ** H
             if ph["out"]:
-                assert ph["a"] == 0 and ph["B"] == 0 and ph["K"] == 6
+                assert ph["a"] == 0 and ph["B"] == 0 and ph["K"] == 7
         assert tickets < 2 ** 32
 
 
