@@ -111,7 +111,13 @@ constexpr int kThreads = 256;
 constexpr int kRounds = (kTileRows + kThreads - 1) / kThreads;  // 9
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
-constexpr int kStageWords = 248;   // per warp: 244 words of 32 rows' bits, padded
+// The last warp of a tile stages the bits of kTileRows % 32 = 11 rows in those
+// rows' 88 words; the staged words, rounded up to whole uint4, fit, and so
+// do the 9 words the list reads from the start of the last row.
+static_assert(kTileRows % 32 == 11, "tile tail");
+static_assert(4 * ((31 + 243 * 11 + 127) / 128) <= 8 * 11, "tail staging fits its rows");
+static_assert((31 + 243 * 10) / 32 + 9 <= 8 * 11, "tail list reads fit its rows");
+static_assert((31 + 243 * 31) / 32 + 9 <= 8 * 32, "list reads fit a warp's rows");
 
 enum PassMode : int { kModeMerge = 0, kModeMergeReduce = 1, kModeReduce = 2, kModeOut = 3 };
 
@@ -237,7 +243,7 @@ struct PassShared {
 };
 
 template <int K, int B, int LOAD, int MODE>
-__global__ void __launch_bounds__(kThreads, (MODE == kModeOut) ? 2 : 3)
+__global__ void __launch_bounds__(kThreads, 3)
 pass_kernel(const __grid_constant__ PassParams P)
 {
     constexpr int RE = (int)pow3(B);
@@ -354,8 +360,7 @@ pass_kernel(const __grid_constant__ PassParams P)
         const uint32_t o = (uint32_t)(bit0 & 31);
         const uint64_t W0 = bit0 >> 5;
         const bool last_tile = (base + R == P.total_rows);
-        uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 2 * R) + wid * kStageWords;
-        uint16_t *const cnt = reinterpret_cast<uint16_t *>(tile + 2 * R) + (kThreads / 32) * kStageWords * 2;
+        uint8_t *const cnt = reinterpret_cast<uint8_t *>(tile + 2 * R);  // primes per row (OUT)
 
 #pragma unroll 1
         for (int rd = 0; rd < kRounds; ++rd) {
@@ -401,14 +406,21 @@ pass_kernel(const __grid_constant__ PassParams P)
 #pragma unroll
                 for (int w = 0; w < kChunkWords; ++w) c += __popc(v[w]);
                 my_count += c;
-                if (ri < R) cnt[ri] = (uint16_t)c;
-                // This warp's 32 rows q0 .. q0+31 are tile bits o + 243*q0 ..:
-                // words S .. S+243 of the tile (S = 243 * q0 / 32), starting
-                // at bit o of word S.
+                if (ri < R) cnt[ri] = (uint8_t)c;  // <= 243
+                // A row is read only by rows of smaller index (its '*'
+                // neighbours lie above it), so once this round's reads are
+                // done its rows' slots are free: each warp stages the dense
+                // bits of its 32 rows there and keeps them for the list.
+                __syncthreads();
                 const int q0 = rd * kThreads + wid * 32;
                 const int nrows = min(32, R - q0);
                 if (nrows > 0) {
-                    for (int i = lane; i < kStageWords; i += 32) stg[i] = 0u;
+                    uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 2 * q0);
+                    // these rows are tile bits o + 243*q0 ..: words S0 .. of the
+                    // bitmap, starting at bit o of word S0
+                    const uint32_t hi_bit = o + 243u * (uint32_t)nrows;  // end of these rows' bits
+                    const int nw4 = (int)((hi_bit + 127u) >> 7);          // uint4 words holding them
+                    for (int i = lane; i < nw4; i += 32) reinterpret_cast<uint4 *>(stg)[i] = make_uint4(0u, 0u, 0u, 0u);
                     __syncwarp();
                     if (ri < R) {
                         const uint32_t lb = o + 243u * (uint32_t)lane;
@@ -429,8 +441,29 @@ pass_kernel(const __grid_constant__ PassParams P)
                     }
                     __syncwarp();
                     const uint64_t S0 = W0 + (uint64_t)243 * (uint64_t)(q0 >> 5);
-                    const uint32_t hi_bit = o + 243u * (uint32_t)nrows;  // end of these rows' bits
-                    for (int j = lane; j < 244; j += 32) {
+                    if (nrows == 32 && ck(P, S0 + 244 <= P.out_alloc_words, S0 + 244)) {
+                        // 32 full rows: words 1 .. 242 hold only these rows' bits;
+                        // word 0 holds them from bit o up, word 243 below bit o.
+                        uint32_t *const dstw = P.out + S0;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int j = 1 + lane + 32 * k;
+                            if (j <= 242) dstw[j] = stg[j];
+                        }
+                        if (lane == 0) {
+                            if (o == 0) {
+                                dstw[0] = stg[0];
+                            } else {
+                                const uint32_t m = 0xffffffffu << o;
+                                atomicAnd(dstw, stg[0] | ~m);
+                                atomicOr(dstw, stg[0] & m);
+                            }
+                        } else if (lane == 1 && o != 0) {
+                            const uint32_t m = (1u << o) - 1u;
+                            atomicAnd(dstw + 243, stg[243] | ~m);
+                            atomicOr(dstw + 243, stg[243] & m);
+                        }
+                    } else for (int j = lane; j < 244; j += 32) {
                         // bits of word j owned by these rows: [lo, hi)
                         const int lo = (j == 0) ? (int)o : 0;
                         int hi = (int)min(hi_bit - 32u * (uint32_t)j, 32u);
@@ -449,7 +482,6 @@ pass_kernel(const __grid_constant__ PassParams P)
                             atomicOr(dst, val & m);
                         }
                     }
-                    __syncwarp();
                 }
             }
         }
@@ -520,14 +552,13 @@ pass_kernel(const __grid_constant__ PassParams P)
                         for (int kk = 0; kk < kPer; ++kk) {
                             const int ri = tid * kPer + kk;
                             if (!cnt[ri]) continue;
-                            // this row's 243 bits, read back from the bitmap
-                            const uint64_t b = (base + (uint64_t)ri) * 243u;
-                            const uint64_t wb = b >> 5;
-                            const uint32_t s = (uint32_t)(b & 31);
+                            // this row's 243 bits, staged in its warp's slots
+                            const uint32_t *const stg = reinterpret_cast<const uint32_t *>(tile + 2 * (ri & ~31));
+                            const uint32_t lb = o + 243u * (uint32_t)(ri & 31);
+                            const uint32_t s = lb & 31;
                             uint32_t words[9];
 #pragma unroll
-                            for (int j = 0; j < 9; ++j)
-                                words[j] = (wb + j < P.out_words) ? P.out[wb + j] : 0u;
+                            for (int j = 0; j < 9; ++j) words[j] = stg[(lb >> 5) + j];
                             const uint32_t rm = S.tile_mask | ((uint32_t)__ldg(&g_tab.m7[ri]) << 5);
                             const uint32_t rv = S.tile_val | ((uint32_t)__ldg(&g_tab.v7[ri]) << 5);
 #pragma unroll
@@ -586,7 +617,7 @@ template <int K, int B, int LOAD, int MODE>
 static cudaError_t launch_pass_k(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
     size_t smem = (size_t)kTileRows * kChunkBytes;
-    if (MODE == kModeOut) smem += (size_t)(kThreads / 32) * kStageWords * 4 + (size_t)kTileRows * 2;
+    if (MODE == kModeOut) smem += (size_t)kTileRows;
     auto kern = pass_kernel<K, B, LOAD, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
