@@ -7,14 +7,23 @@
 // group digits (a .. a+K-1) and 7-K inner digits (0 .. 6-K, contiguous rows)
 // vary; every other high digit is fixed per tile.
 //
+// A thread works on a unit: the three tile rows that differ only in tile
+// digit 0 (three consecutive rows of the state).  They share every other
+// digit, so the neighbour arithmetic of a digit is done once for three rows,
+// and when tile digit 0 is a group digit (the bitmap pass) its Reduce is done
+// in registers.  Unit u holds tile rows 3u .. 3u+2; its digits are tile
+// digits 1..6.
+//
 // Per tile:
-//   load   truth-table words (first pass), the rows whose group digits are
-//          0/1 (Merge input), or all rows, into shared memory (cp.async);
+//   load   the first pass reads truth-table words (tt_pass_kernel); the others
+//          read the units whose group digits are 0/1 (Merge input) or all
+//          units into shared memory (cp.async);
 //   Merge  the group digits one after another (Merge of Section 4.1: the
 //          '*' row becomes the AND of its 0 row and 1 row; '*' rows of an
-//          unmerged digit are zero, so assignment equals the paper's OR);
+//          unmerged digit are zero in the state, so assignment equals the
+//          paper's OR);
 //   Reduce the group digits and the pass's chunk digits, every row read from
-//          the tile as loaded (Reduce of Section 4.1: a cell loses its bit
+//          the tile as merged (Reduce of Section 4.1: a cell loses its bit
 //          when its '*' neighbour in a reduced digit is set).  Reducing digits
 //          in groups, each group reading the state the previous groups left,
 //          gives the paper's result: a cube with an implicant one-digit
@@ -23,9 +32,9 @@
 //          extension of the cube in an earlier group), and primes are never
 //          cleared;
 //   store  rows back to the state, or, in the last pass, the dense bitmap
-//          (each warp funnel-shifts its 32 rows into place in shared memory),
-//          the count, and the (mask, value) list placed by a decoupled
-//          look-back over the tiles in rho order.
+//          (each warp funnel-shifts its 96 rows into their own, no longer
+//          needed, slots of the tile), the count, and the (mask, value) list
+//          placed by a decoupled look-back over the tiles in rho order.
 //
 // Every global index is checked against its buffer before the access (ck):
 // a bad one is recorded in the error word and the access skipped.
@@ -38,30 +47,32 @@ namespace dqmc {
 
 static __constant__ MaskTable kMasksP = make_mask_table();
 
-// Lookup tables over the 7 digits of a tile and the 5 chunk digits.
+constexpr int kUnits = kTileRows / 3;  // 729 units of three rows per tile
+// Shared memory of a unit pass: the tile (6 uint4 per unit), then one unit of
+// zeros that stands for the '*' neighbour a '*' digit does not have, then
+// (bitmap pass) one byte per row.
+constexpr int kZeroSlot = 6 * kUnits;
+constexpr size_t kUnitSmem = (size_t)(6 * kUnits + 6) * 16;
+
+// Lookup tables over tile units and the 5 chunk digits.
 struct PassTables {
-    uint8_t has_star[kTileRows];   // the index has a '*' digit
-    uint8_t m7[kTileRows];         // bit d: digit d is 0 or 1 (a literal)
-    uint8_t v7[kTileRows];         // bit d: digit d is 1
-    uint8_t t5m[243], t5v[243];    // the same for the 5 chunk digits
-    uint16_t sp3[128];             // sum of 3^d over the set bits d of the index
+    uint16_t code[kUnits];      // bit d (d < 6): unit digit d is 0/1; bit 8+d: it is 1
+    uint16_t c5[243];           // chunk cell q: bits 0..4 literal digits, bits 8..12 digits = 1
+    uint16_t sp3[128];          // sum of 3^d over the set bits d of the index
 };
 
 __host__ __device__ constexpr PassTables make_pass_tables()
 {
     PassTables t{};
-    for (int i = 0; i < kTileRows; ++i) {
-        int q = i, star = 0, m = 0, v = 0;
-        for (int d = 0; d < 7; ++d) {
+    for (int u = 0; u < kUnits; ++u) {
+        int q = u, m = 0, v = 0;
+        for (int d = 0; d < 6; ++d) {
             const int dg = q % 3;
             q /= 3;
-            if (dg == 2) star = 1;
-            else m |= 1 << d;
+            if (dg != 2) m |= 1 << d;
             if (dg == 1) v |= 1 << d;
         }
-        t.has_star[i] = (uint8_t)star;
-        t.m7[i] = (uint8_t)m;
-        t.v7[i] = (uint8_t)v;
+        t.code[u] = (uint16_t)(m | (v << 8));
     }
     for (int i = 0; i < 243; ++i) {
         int q = i, m = 0, v = 0;
@@ -71,8 +82,7 @@ __host__ __device__ constexpr PassTables make_pass_tables()
             if (dg != 2) m |= 1 << d;
             if (dg == 1) v |= 1 << d;
         }
-        t.t5m[i] = (uint8_t)m;
-        t.t5v[i] = (uint8_t)v;
+        t.c5[i] = (uint16_t)(m | (v << 8));
     }
     for (int i = 0; i < 128; ++i) {
         int r = 0, w = 1, x = i;
@@ -103,21 +113,22 @@ struct PassParams {
     uint64_t wait_ns;
     uint64_t w_g;               // 3^a
     uint32_t nmask;             // (1 << n) - 1
-    int H, chunk_mask, slot;
+    int H, slot;
     FixedDigits fix;            // digits fixed per tile, ascending
 };
 
 constexpr int kThreads = 256;
-constexpr int kRounds = (kTileRows + kThreads - 1) / kThreads;  // 9
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
-// The last warp of a tile stages the bits of kTileRows % 32 = 11 rows in those
-// rows' 88 words; the staged words, rounded up to whole uint4, fit, and so
-// do the 9 words the list reads from the start of the last row.
-static_assert(kTileRows % 32 == 11, "tile tail");
-static_assert(4 * ((31 + 243 * 11 + 127) / 128) <= 8 * 11, "tail staging fits its rows");
-static_assert((31 + 243 * 10) / 32 + 9 <= 8 * 11, "tail list reads fit its rows");
-static_assert((31 + 243 * 31) / 32 + 9 <= 8 * 32, "list reads fit a warp's rows");
+
+// Bitmap staging (last pass): a warp's 32 units are 96 rows = 768 words of
+// the tile; their 32 * 729 bits, starting at bit o < 32, take 730 words.  The
+// last warp of a tile has 729 - 22 * 32 = 25 units (600 words).
+static_assert(kUnits == 22 * 32 + 25, "tile units");
+static_assert((31 + 32 * 729 + 31) / 32 <= 24 * 32, "full staging fits its rows");
+static_assert(4 * ((31 + 25 * 729 + 127) / 128) <= 24 * 25, "tail staging fits its rows");
+static_assert((31 + 729 * 24 + 486) / 32 + 9 <= 24 * 25, "tail list reads fit its rows");
+static_assert((31 + 729 * 31 + 486) / 32 + 9 <= 24 * 32, "list reads fit a warp's rows");
 
 enum PassMode : int { kModeMerge = 0, kModeMergeReduce = 1, kModeReduce = 2, kModeOut = 3 };
 
@@ -135,6 +146,13 @@ __device__ __forceinline__ bool ck(const PassParams &P, bool cond, uint64_t idx)
     return false;
 }
 
+// Shared-memory slot (uint4) of 16-byte piece c (row c/2, half c%2) of unit u.
+// Swapping the halves of every other group of four units keeps the eight
+// lanes of a quarter-warp on eight different 16-byte bank groups when they
+// read the same piece of consecutive units.
+__device__ __forceinline__ int uslot(int u, int c) { return 6 * u + (c ^ ((u >> 2) & 1)); }
+
+// The first pass's tile layout: row r, half h.
 __device__ __forceinline__ int slotp(int r, int h) { return 2 * r + (h ^ ((r >> 2) & 1)); }
 
 __device__ __forceinline__ void cp_async16p(void *smem_dst, const void *gmem_src)
@@ -155,13 +173,15 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64p(const unsigned lo
     return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
-__device__ __forceinline__ void chunk_reduce_masked_p(const uint32_t (&v)[kChunkWords],
-                                                      uint32_t (&acc)[kChunkWords], int mask)
+// Reduce of the chunk digits in CM (bit i = chunk digit i): acc gains every
+// cell whose '*' neighbour in such a digit is set in v.
+template <int CM>
+__device__ __forceinline__ void chunk_reduce_p(const uint32_t (&v)[kChunkWords], uint32_t (&acc)[kChunkWords])
 {
     static_for<0, kChunkDigits>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int d = (int)pow3(i);
-        if ((mask >> i) & 1) {
+        if constexpr ((CM >> i) & 1) {
             uint32_t y[kChunkWords];
 #pragma unroll
             for (int w = 0; w < kChunkWords; ++w) y[w] = v[w] & kMasksP.m[kChunkDigits][i][2][w];
@@ -234,41 +254,36 @@ __device__ unsigned long long lookback_p(const PassParams &P, uint64_t T, bool &
 }
 
 struct PassShared {
-    FixedDigits fix;
+    alignas(8) unsigned char fix_raw[sizeof(FixedDigits)];  // FixedDigits, copied from the parameters
     uint64_t base, ttb, tile;
     unsigned long long excl;
     uint32_t warp_tot[kThreads / 32];
     uint32_t tile_mask, tile_val;
     int list_ok;
+    __device__ const FixedDigits &fix() const { return *reinterpret_cast<const FixedDigits *>(fix_raw); }
 };
 
-template <int K, int B, int LOAD, int MODE>
-__global__ void __launch_bounds__(kThreads, 3)
-pass_kernel(const __grid_constant__ PassParams P)
+// Tile id -> first state row (S.base) and first truth-table word (S.ttb).
+// With kTicket and a list, tiles take ids in the order they start, so a
+// tile's look-back waits only on tiles already running.
+template <bool kTicket>
+__device__ __forceinline__ void decode_tile(const PassParams &P, PassShared &S)
 {
-    constexpr int RE = (int)pow3(B);
-    constexpr int RG = (int)pow3(K);
-    constexpr int R = RG * RE;
-    constexpr int NB = 1 << K;
-    static_assert(R == kTileRows, "tiles are 2187 rows");
-    extern __shared__ uint4 tile[];
-    __shared__ PassShared S;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-
-    // ---------------------------------------------------------------- tile
+    const int tid = threadIdx.x;
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&P.fix);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&S.fix);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(S.fix_raw);
         for (int i = tid; i < (int)(sizeof(FixedDigits) / 4); i += kThreads) dst[i] = src[i];
     }
     __syncthreads();
     if (tid == 0) {
+        const FixedDigits &f = S.fix();
         uint64_t t = blockIdx.x;
-        if (MODE == kModeOut && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);  // tiles start in rho order
+        if (kTicket && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
         uint64_t base = 0, ttb = 0, x = t;
-        for (int i = 0; i < S.fix.n; ++i) {
+        for (int i = 0; i < f.n; ++i) {
             uint64_t d;
-            if (S.fix.r[i] == 2) {
+            if (f.r[i] == 2) {
                 d = x & 1u;
                 x >>= 1;
             } else {
@@ -276,41 +291,113 @@ pass_kernel(const __grid_constant__ PassParams P)
                 d = x - 3u * q;
                 x = q;
             }
-            base += d * S.fix.w3[i];
-            ttb += d * S.fix.w2[i];
+            base += d * f.w3[i];
+            ttb += d * f.w2[i];
         }
         S.base = base;
         S.ttb = ttb;
         S.tile = t;
     }
     __syncthreads();
+}
+
+// ------------------------------------------------------------ first pass
+// Truth table -> rows with the chunk digits and tile digits 0..6 merged
+// (digits >= 7 are still 0/1: their '*' rows are not written).
+__global__ void __launch_bounds__(kThreads, 3) tt_pass_kernel(const __grid_constant__ PassParams P)
+{
+    constexpr int R = kTileRows;
+    extern __shared__ uint4 tile[];
+    __shared__ PassShared S;
+    const int tid = threadIdx.x;
+    decode_tile<false>(P, S);
     const uint64_t base = S.base, ttb = S.ttb;
+
+    for (int gb = tid; gb < (1 << kTileDigits); gb += kThreads) {
+        if (!ck(P, ttb + gb < P.tt_words, ttb + gb)) continue;
+        uint32_t x = __ldg(P.on + ttb + gb);
+        if (P.dc) x |= __ldg(P.dc + ttb + gb);
+        uint32_t v[kChunkWords];
+        chunk_from_word_p(x, v);
+        const int r = __ldg(&g_tab.sp3[gb]);
+        tile[slotp(r, 0)] = make_uint4(v[0], v[1], v[2], v[3]);
+        tile[slotp(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
+    }
+    __syncthreads();
+    static_for<0, kTileDigits>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        constexpr int dj = (int)pow3(j);
+        constexpr int items = dj * (1 << (kTileDigits - 1 - j)) * 2;
+        for (int it = tid; it < items; it += kThreads) {
+            const int h = it & 1;
+            const int r = it >> 1;
+            const int lo = r % dj;
+            const int hb = r / dj;
+            const int r0 = lo + 3 * dj * (int)__ldg(&g_tab.sp3[hb]);
+            const uint4 s0 = tile[slotp(r0, h)];
+            const uint4 s1 = tile[slotp(r0 + dj, h)];
+            tile[slotp(r0 + 2 * dj, h)] = make_uint4(s0.x & s1.x, s0.y & s1.y, s0.z & s1.z, s0.w & s1.w);
+        }
+        __syncthreads();
+    });
+    for (int pc = tid; pc < R * 2; pc += kThreads) {
+        const int h = pc & 1, ri = pc >> 1;
+        const uint64_t row = base + ri;
+        if (!ck(P, row < P.state_rows, row)) continue;
+        P.state[2 * row + h] = tile[slotp(ri, h)];
+    }
+}
+
+// ------------------------------------------------------------ unit passes
+//
+// B >= 1: tile row e + 3^B g (inner e < 3^B, group index g < 3^K); unit
+//         u = eh + RU g holds e = 3 eh .. 3 eh + 2 (RU = 3^(B-1)); its group
+//         digits are unit digits B-1 .. 5.
+// B == 0: the bitmap pass (a = 0): unit u holds tile rows 3u .. 3u+2, i.e.
+//         state rows base + 3u + k; tile digit 0 and unit digits 0 .. 5 are
+//         the group digits.
+template <int K, int B, int LOAD, int MODE, int CM, bool STAGE>
+__global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_constant__ PassParams P)
+{
+    static_assert(K + B == kTileDigits, "tiles are 3^7 rows");
+    static_assert(B >= 1 || (MODE == kModeOut && LOAD == kLoadFull), "B = 0 only in the bitmap pass");
+    constexpr int RU = (B == 0) ? 1 : (int)pow3(B - 1);
+    constexpr int D0 = (B == 0) ? 0 : B - 1;    // lowest group unit digit
+    constexpr int NB = 1 << K;
+    extern __shared__ uint4 tile[];
+    __shared__ PassShared S;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    decode_tile<MODE == kModeOut>(P, S);
+    const uint64_t base = S.base;
     const uint64_t w_g = P.w_g;
     uint4 *const state = P.state;
     const uint64_t state_rows = P.state_rows;
+    // first state row of unit u
+    auto unit_row = [&](int u) -> uint64_t {
+        if constexpr (B == 0) {
+            return base + 3u * (uint64_t)u;
+        } else {
+            const int g = u / RU, eh = u - g * RU;
+            return base + 3u * (uint64_t)eh + (uint64_t)g * w_g;
+        }
+    };
 
     // ---------------------------------------------------------------- load
-    if constexpr (LOAD == kLoadTT) {
-        for (int gb = tid; gb < NB; gb += kThreads) {
-            if (!ck(P, ttb + gb < P.tt_words, ttb + gb)) continue;
-            uint32_t x = __ldg(P.on + ttb + gb);
-            if (P.dc) x |= __ldg(P.dc + ttb + gb);
-            uint32_t v[kChunkWords];
-            chunk_from_word_p(x, v);
-            const int r = __ldg(&g_tab.sp3[gb]);
-            tile[slotp(r, 0)] = make_uint4(v[0], v[1], v[2], v[3]);
-            tile[slotp(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
+    {
+        constexpr int units_in = (LOAD == kLoadSparse) ? NB * RU : kUnits;
+        for (int p = tid; p < units_in * 6; p += kThreads) {
+            const int q = p / 6, c = p - 6 * q;
+            int u = q;
+            if constexpr (LOAD == kLoadSparse) {
+                const int gb = q / RU, eh = q - gb * RU;
+                u = eh + RU * (int)__ldg(&g_tab.sp3[gb]);
+            }
+            const uint64_t row0 = unit_row(u);
+            if (!ck(P, row0 + 2 < state_rows, row0 + 2)) continue;
+            cp_async16p(&tile[uslot(u, c)], &state[2 * row0 + c]);
         }
-    } else {
-        constexpr int rows_in = (LOAD == kLoadSparse) ? NB * RE : R;
-        for (int pc = tid; pc < rows_in * 2; pc += kThreads) {
-            const int h = pc & 1, ri = pc >> 1;
-            const int q = ri / RE, e = ri - q * RE;
-            const int g = (LOAD == kLoadSparse) ? (int)__ldg(&g_tab.sp3[q]) : q;
-            const uint64_t row = base + e + (uint64_t)g * w_g;
-            if (!ck(P, row < state_rows, row)) continue;
-            cp_async16p(&tile[slotp(g * RE + e, h)], &state[2 * row + h]);
-        }
+        if (tid < 6) tile[kZeroSlot + tid] = make_uint4(0u, 0u, 0u, 0u);
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
     __syncthreads();
@@ -318,138 +405,192 @@ pass_kernel(const __grid_constant__ PassParams P)
     // --------------------------------------------------------------- Merge
     if constexpr (MODE == kModeMerge || MODE == kModeMergeReduce) {
         static_for<0, K>([&](auto J) {
+            constexpr int d = D0 + decltype(J)::value;
+            constexpr int Dd = (int)pow3(d);
+            // units whose digit d is '*' and whose later group digits are
+            // still 0/1: RU * 3^j * 2^(K-1-j) <= 243 of them
             constexpr int j = decltype(J)::value;
-            constexpr int dj = (int)pow3(j);
-            constexpr int items = dj * (1 << (K - 1 - j)) * RE * 2;
-            for (int it = tid; it < items; it += kThreads) {
-                const int h = it & 1;
-                int r = it >> 1;
-                const int e = r % RE;
-                r /= RE;
-                const int lo = r % dj;
-                const int hb = r / dj;
-                const int g = lo + 3 * dj * (int)__ldg(&g_tab.sp3[hb]);
-                const int r0 = g * RE + e;
-                const uint4 s0 = tile[slotp(r0, h)];
-                const uint4 s1 = tile[slotp(r0 + dj * RE, h)];
-                tile[slotp(r0 + 2 * dj * RE, h)] = make_uint4(s0.x & s1.x, s0.y & s1.y, s0.z & s1.z, s0.w & s1.w);
+            constexpr int Dj = (int)pow3(j);
+            constexpr int items = RU * Dj * (1 << (K - 1 - j));
+            static_assert(items <= kThreads, "one unit per thread");
+            if (tid < items) {
+                const int eh = tid % RU, rest = tid / RU;
+                const int lo = rest % Dj, hb = rest / Dj;
+                const int u = eh + RU * (lo + 2 * Dj + 3 * Dj * (int)__ldg(&g_tab.sp3[hb]));
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const uint4 s0 = tile[uslot(u - 2 * Dd, c)];
+                    const uint4 s1 = tile[uslot(u - Dd, c)];
+                    tile[uslot(u, c)] = make_uint4(s0.x & s1.x, s0.y & s1.y, s0.z & s1.z, s0.w & s1.w);
+                }
             }
             __syncthreads();
         });
     }
 
     if constexpr (MODE == kModeMerge) {
-        // Write the rows the Merge created (rows whose group digits are all
-        // 0/1 came from the state unchanged), or all rows when they came from
-        // the truth table.
-        for (int pc = tid; pc < R * 2; pc += kThreads) {
-            const int h = pc & 1, ri = pc >> 1;
-            const int g = ri / RE, e = ri - g * RE;
-            if (LOAD != kLoadTT && !__ldg(&g_tab.has_star[g])) continue;
-            const uint64_t row = base + e + (uint64_t)g * w_g;
-            if (!ck(P, row < state_rows, row)) continue;
-            state[2 * row + h] = tile[slotp(ri, h)];
+        // Write the units the Merge created (a '*' in a group digit); the
+        // others came from the state unchanged.
+        constexpr uint32_t gmask = (0x3fu >> D0) << D0;
+        for (int p = tid; p < kUnits * 6; p += kThreads) {
+            const int u = p / 6, c = p - 6 * u;
+            if (!(~(uint32_t)__ldg(&g_tab.code[u]) & gmask)) continue;
+            const uint64_t row0 = unit_row(u);
+            if (!ck(P, row0 + 2 < state_rows, row0 + 2)) continue;
+            state[2 * row0 + c] = tile[uslot(u, c)];
         }
         return;
     } else {
-        // ------------------------------------------------------- Reduce rows
-        const int cmask = P.chunk_mask;
+        // ------------------------------------------------------- Reduce units
         uint32_t my_count = 0;
-        // out: this tile's bits are bits bit0 .. bit0 + R*243 - 1 of the bitmap
+        // out: this tile's bits are bits bit0 .. bit0 + 2187*243 - 1 of the bitmap
         const uint64_t bit0 = base * 243u;
         const uint32_t o = (uint32_t)(bit0 & 31);
         const uint64_t W0 = bit0 >> 5;
-        const bool last_tile = (base + R == P.total_rows);
-        uint8_t *const cnt = reinterpret_cast<uint8_t *>(tile + 2 * R);  // primes per row (OUT)
+        const bool last_tile = (base + kTileRows == P.total_rows);
+        uint8_t *const cnt = reinterpret_cast<uint8_t *>(tile + kZeroSlot + 6);  // primes per row (out)
 
+        // A unit is read only by units of smaller or equal index (its '*'
+        // neighbours lie above it), so once a round's reads of a row are
+        // done, that row of the round's units is free: the reduce passes put
+        // the reduced row back in place, the bitmap pass stages dense bits there.
 #pragma unroll 1
-        for (int rd = 0; rd < kRounds; ++rd) {
-            const int ri = rd * kThreads + tid;
-            uint32_t v[kChunkWords];
-#pragma unroll
-            for (int w = 0; w < kChunkWords; ++w) v[w] = 0;
-            if (ri < R) {
-                const uint4 q0 = tile[slotp(ri, 0)], q1 = tile[slotp(ri, 1)];
-                v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w;
-                v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
+        for (int rd = 0; rd < 3; ++rd) {
+            const int u = rd * kThreads + tid;
+            const bool valid = u < kUnits;
+            // Slots of the '*' neighbour of u in each group digit d: digit
+            // 0 -> u + 2*3^d, 1 -> u + 3^d, '*' -> the zero unit.
+            // se: even pieces (first row halves), so: odd pieces.
+            int se[6 - D0], so[6 - D0];
+            {
+                const uint32_t code = valid ? (uint32_t)__ldg(&g_tab.code[u]) : 0u;
+                static_for<D0, 6>([&](auto Dg) {
+                    constexpr int d = decltype(Dg)::value;
+                    constexpr int Dd = (int)pow3(d);
+                    const uint32_t lit = (code >> d) & 1u, one = (code >> (8 + d)) & 1u;
+                    const int nb = u + (int)(2u - one) * Dd;
+                    const int sw = (nb >> 2) & 1;
+                    se[d - D0] = lit ? 6 * nb + sw : kZeroSlot;
+                    so[d - D0] = lit ? 6 * nb + 1 - sw : kZeroSlot + 1;
+                });
+            }
+            // row k of the unit: OR of its '*' neighbours, chunk digits,
+            // then the row loses those cells
+            auto finish_row = [&](int k, uint32_t (&xr)[kChunkWords]) {
                 uint32_t acc[kChunkWords];
+                if (B == 0 && k < 2) {
+                    // tile digit 0: rows 0 and 1 lose what row 2 ('*') holds
+                    const uint4 q0 = tile[uslot(u, 4)], q1 = tile[uslot(u, 5)];
+                    acc[0] = q0.x; acc[1] = q0.y; acc[2] = q0.z; acc[3] = q0.w;
+                    acc[4] = q1.x; acc[5] = q1.y; acc[6] = q1.z; acc[7] = q1.w;
+                } else {
 #pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) acc[w] = 0;
-                int gg = ri / RE;
+                    for (int w = 0; w < kChunkWords; ++w) acc[w] = 0u;
+                }
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const int dg = gg % 3;
-                    gg /= 3;
-                    if (dg != 2) {
-                        const int nb = ri + (2 - dg) * (int)pow3(j) * RE;
-                        const uint4 a0 = tile[slotp(nb, 0)], a1 = tile[slotp(nb, 1)];
-                        acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
-                        acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
+                for (int i = 0; i < 6 - D0; ++i) {
+                    const uint4 a0 = tile[se[i] + 2 * k], a1 = tile[so[i] + 2 * k];
+                    acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
+                    acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
+                }
+                const uint4 q0 = tile[uslot(u, 2 * k)], q1 = tile[uslot(u, 2 * k + 1)];
+                xr[0] = q0.x; xr[1] = q0.y; xr[2] = q0.z; xr[3] = q0.w;
+                xr[4] = q1.x; xr[5] = q1.y; xr[6] = q1.z; xr[7] = q1.w;
+                chunk_reduce_p<CM>(xr, acc);
+#pragma unroll
+                for (int w = 0; w < kChunkWords; ++w) xr[w] &= ~acc[w];
+            };
+
+            if constexpr (MODE != kModeOut && STAGE) {
+                // Row k of a unit is read only while rows k are reduced: the
+                // reduced row goes back to its slot after this round's reads.
+#pragma unroll 1
+                for (int k = 0; k < 3; ++k) {
+                    uint32_t xr[kChunkWords];
+                    if (valid) finish_row(k, xr);
+                    __syncthreads();
+                    if (valid) {
+                        tile[uslot(u, 2 * k)] = make_uint4(xr[0], xr[1], xr[2], xr[3]);
+                        tile[uslot(u, 2 * k + 1)] = make_uint4(xr[4], xr[5], xr[6], xr[7]);
                     }
                 }
-                if (cmask) chunk_reduce_masked_p(v, acc, cmask);
-#pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
-            }
-            if constexpr (MODE != kModeOut) {
-                if (ri < R) {
-                    const int g = ri / RE, e = ri - g * RE;
-                    const uint64_t row = base + e + (uint64_t)g * w_g;
-                    if (ck(P, row < state_rows, row)) {
-                        state[2 * row] = make_uint4(v[0], v[1], v[2], v[3]);
-                        state[2 * row + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+            } else if constexpr (MODE != kModeOut) {
+                // reduced rows straight to the state
+                if (valid) {
+                    const uint64_t row0 = unit_row(u);
+                    const bool row_ok = ck(P, row0 + 2 < state_rows, row0 + 2);
+#pragma unroll 1
+                    for (int k = 0; k < 3; ++k) {
+                        uint32_t xr[kChunkWords];
+                        finish_row(k, xr);
+                        if (row_ok) {
+                            state[2 * (row0 + k)] = make_uint4(xr[0], xr[1], xr[2], xr[3]);
+                            state[2 * (row0 + k) + 1] = make_uint4(xr[4], xr[5], xr[6], xr[7]);
+                        }
                     }
                 }
             } else {
-                // ------------------------------------- count and dense bits
-                uint32_t c = 0;
+                uint32_t x[3][kChunkWords];
+                if (valid) {
 #pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) c += __popc(v[w]);
-                my_count += c;
-                if (ri < R) cnt[ri] = (uint8_t)c;  // <= 243
-                // A row is read only by rows of smaller index (its '*'
-                // neighbours lie above it), so once this round's reads are
-                // done its rows' slots are free: each warp stages the dense
-                // bits of its 32 rows there and keeps them for the list.
+                    for (int k = 0; k < 3; ++k) finish_row(k, x[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+#pragma unroll
+                        for (int w = 0; w < kChunkWords; ++w) x[k][w] = 0u;
+                }
+                // ------------------------------------- count and dense bits
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    uint32_t c = 0;
+#pragma unroll
+                    for (int w = 0; w < kChunkWords; ++w) c += __popc(x[k][w]);
+                    my_count += c;
+                    if (u < kUnits) cnt[3 * u + k] = (uint8_t)c;  // <= 243
+                }
+                // every read of this round's units is done: each warp stages
+                // the dense bits of its 32 units in their slots and keeps them
+                // for the list
                 __syncthreads();
-                const int q0 = rd * kThreads + wid * 32;
-                const int nrows = min(32, R - q0);
-                if (nrows > 0) {
-                    uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 2 * q0);
-                    // these rows are tile bits o + 243*q0 ..: words S0 .. of the
+                const int U0 = rd * kThreads + wid * 32;
+                const int nun = min(32, kUnits - U0);
+                if (nun > 0) {
+                    uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 6 * U0);
+                    // these units are tile bits 729*U0 ..: words S0 .. of the
                     // bitmap, starting at bit o of word S0
-                    const uint32_t hi_bit = o + 243u * (uint32_t)nrows;  // end of these rows' bits
-                    const int nw4 = (int)((hi_bit + 127u) >> 7);          // uint4 words holding them
+                    const uint32_t hi_bit = o + 729u * (uint32_t)nun;   // end of these units' bits
+                    const int nw4 = (int)((hi_bit + 127u) >> 7);        // uint4 words holding them
                     for (int i = lane; i < nw4; i += 32) reinterpret_cast<uint4 *>(stg)[i] = make_uint4(0u, 0u, 0u, 0u);
                     __syncwarp();
-                    if (ri < R) {
-                        const uint32_t lb = o + 243u * (uint32_t)lane;
-                        const uint32_t k0 = lb >> 5, s = lb & 31;
-                        const uint32_t cw = (s + 243u + 31u) >> 5;  // 8 or 9 words
-                        uint32_t w9[9];
-                        w9[0] = v[0] << s;
+                    if (u < kUnits) {
 #pragma unroll
-                        for (int j = 1; j < 8; ++j) w9[j] = __funnelshift_l(v[j - 1], v[j], s);
-                        w9[8] = __funnelshift_l(v[7], 0u, s);
-                        atomicOr(&stg[k0], w9[0]);
+                        for (int k = 0; k < 3; ++k) {
+                            const uint32_t lb = o + 729u * (uint32_t)lane + 243u * (uint32_t)k;
+                            const uint32_t k0 = lb >> 5, s = lb & 31;
+                            const uint32_t cw = (s + 243u + 31u) >> 5;  // 8 or 9 words
+                            uint32_t w9[9];
+                            w9[0] = x[k][0] << s;
 #pragma unroll
-                        for (int j = 1; j < 8; ++j) {
-                            if ((uint32_t)j < cw - 1) stg[k0 + j] = w9[j];
-                            else if ((uint32_t)j == cw - 1) atomicOr(&stg[k0 + j], w9[j]);
+                            for (int j = 1; j < 8; ++j) w9[j] = __funnelshift_l(x[k][j - 1], x[k][j], s);
+                            w9[8] = __funnelshift_l(x[k][7], 0u, s);
+                            atomicOr(&stg[k0], w9[0]);
+#pragma unroll
+                            for (int j = 1; j < 8; ++j) {
+                                if ((uint32_t)j < cw - 1) stg[k0 + j] = w9[j];
+                                else if ((uint32_t)j == cw - 1) atomicOr(&stg[k0 + j], w9[j]);
+                            }
+                            if (cw == 9) atomicOr(&stg[k0 + 8], w9[8]);
                         }
-                        if (cw == 9) atomicOr(&stg[k0 + 8], w9[8]);
                     }
                     __syncwarp();
-                    const uint64_t S0 = W0 + (uint64_t)243 * (uint64_t)(q0 >> 5);
-                    if (nrows == 32 && ck(P, S0 + 244 <= P.out_alloc_words, S0 + 244)) {
-                        // 32 full rows: words 1 .. 242 hold only these rows' bits;
-                        // word 0 holds them from bit o up, word 243 below bit o.
+                    const uint64_t S0 = W0 + (uint64_t)729 * (uint64_t)(U0 >> 5);
+                    if (nun == 32 && ck(P, S0 + 730 <= P.out_alloc_words, S0 + 730)) {
+                        // 32 full units: words 1 .. 728 hold only their bits;
+                        // word 0 holds them from bit o up, word 729 below bit o.
                         uint32_t *const dstw = P.out + S0;
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int j = 1 + lane + 32 * k;
-                            if (j <= 242) dstw[j] = stg[j];
-                        }
+#pragma unroll 4
+                        for (int j = 1 + lane; j <= 728; j += 32) dstw[j] = stg[j];
                         if (lane == 0) {
                             if (o == 0) {
                                 dstw[0] = stg[0];
@@ -460,39 +601,51 @@ pass_kernel(const __grid_constant__ PassParams P)
                             }
                         } else if (lane == 1 && o != 0) {
                             const uint32_t m = (1u << o) - 1u;
-                            atomicAnd(dstw + 243, stg[243] | ~m);
-                            atomicOr(dstw + 243, stg[243] & m);
+                            atomicAnd(dstw + 729, stg[729] | ~m);
+                            atomicOr(dstw + 729, stg[729] & m);
                         }
-                    } else for (int j = lane; j < 244; j += 32) {
-                        // bits of word j owned by these rows: [lo, hi)
-                        const int lo = (j == 0) ? (int)o : 0;
-                        int hi = (int)min(hi_bit - 32u * (uint32_t)j, 32u);
-                        if ((uint32_t)(32 * j) >= hi_bit) hi = 0;
-                        const uint64_t wi = S0 + (uint64_t)j;
-                        if (last_tile && wi == P.out_words - 1 && hi > lo) hi = 32;  // bits past 3^n are 0
-                        if (hi <= lo) continue;
-                        if (!ck(P, wi < P.out_alloc_words, wi)) continue;
-                        const uint32_t val = stg[j];
-                        uint32_t *dst = P.out + wi;
-                        if (lo == 0 && hi == 32) {
-                            *dst = val;
-                        } else {
-                            const uint32_t m = (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u)) & (0xffffffffu << lo);
-                            atomicAnd(dst, val | ~m);
-                            atomicOr(dst, val & m);
+                    } else {
+                        const int nw = (int)((hi_bit + 31u) >> 5);
+                        for (int j = lane; j < nw; j += 32) {
+                            // bits of word j owned by these units: [lo, hi)
+                            const int lo = (j == 0) ? (int)o : 0;
+                            const int hi = (int)min(hi_bit - 32u * (uint32_t)j, 32u);
+                            const uint64_t wi = S0 + (uint64_t)j;
+                            const int hi2 = (last_tile && wi == P.out_words - 1) ? 32 : hi;  // bits past 3^n are 0
+                            if (hi2 <= lo) continue;
+                            if (!ck(P, wi < P.out_alloc_words, wi)) continue;
+                            const uint32_t val = stg[j];
+                            uint32_t *dst = P.out + wi;
+                            if (lo == 0 && hi2 == 32) {
+                                *dst = val;
+                            } else {
+                                const uint32_t m = (hi2 == 32 ? 0xffffffffu : ((1u << hi2) - 1u)) & (0xffffffffu << lo);
+                                atomicAnd(dst, val | ~m);
+                                atomicOr(dst, val & m);
+                            }
                         }
                     }
                 }
             }
         }
 
-        if constexpr (MODE == kModeOut) {
+        if constexpr (MODE != kModeOut && STAGE) {
+            // reduced tile -> state, consecutive lanes on consecutive 16-byte
+            // pieces of a unit's three rows
+            __syncthreads();
+            for (int p = tid; p < kUnits * 6; p += kThreads) {
+                const int uu = p / 6, c = p - 6 * uu;
+                const uint64_t row0 = unit_row(uu);
+                if (!ck(P, row0 + 2 < state_rows, row0 + 2)) continue;
+                state[2 * row0 + c] = tile[uslot(uu, c)];
+            }
+        } else if constexpr (MODE == kModeOut) {
             if (last_tile)
                 for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += kThreads) P.out[w] = 0u;
             // tile count
-            uint32_t x = my_count;
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            if (lane == 0) S.warp_tot[wid] = x;
+            uint32_t xs = my_count;
+            for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+            if (lane == 0) S.warp_tot[wid] = xs;
             __syncthreads();
             uint32_t tile_total = 0;
 #pragma unroll
@@ -530,11 +683,10 @@ pass_kernel(const __grid_constant__ PassParams P)
                 }
                 __syncthreads();
                 if (S.list_ok) {
-                    // rows 9t .. 9t+8 belong to thread t < 243: prefix over rows
-                    constexpr int kPer = kTileRows / 243;  // 9
+                    // units 3t .. 3t+2 (rows 9t .. 9t+8) belong to thread t < 243
                     uint32_t mine = 0;
                     if (tid < 243)
-                        for (int k = 0; k < kPer; ++k) mine += cnt[tid * kPer + k];
+                        for (int r = 0; r < 9; ++r) mine += cnt[9 * tid + r];
                     uint32_t incl = mine;
                     for (int off = 1; off < 32; off <<= 1) {
                         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
@@ -549,30 +701,36 @@ pass_kernel(const __grid_constant__ PassParams P)
                     const uint64_t cap = P.cap;
                     const uint32_t nmask = P.nmask;
                     if (tid < 243 && mine && k < cap) {
-                        for (int kk = 0; kk < kPer; ++kk) {
-                            const int ri = tid * kPer + kk;
-                            if (!cnt[ri]) continue;
-                            // this row's 243 bits, staged in its warp's slots
-                            const uint32_t *const stg = reinterpret_cast<const uint32_t *>(tile + 2 * (ri & ~31));
-                            const uint32_t lb = o + 243u * (uint32_t)(ri & 31);
-                            const uint32_t s = lb & 31;
-                            uint32_t words[9];
+                        for (int uu = 0; uu < 3; ++uu) {
+                            const int u = 3 * tid + uu;
+                            const uint32_t code = __ldg(&g_tab.code[u]);
+                            // this unit's bits, staged in its warp's slots
+                            const uint32_t *const stg = reinterpret_cast<const uint32_t *>(tile + 6 * (u & ~31));
+                            for (int kr = 0; kr < 3; ++kr) {
+                                if (!cnt[3 * u + kr]) continue;
+                                const uint32_t lb = o + 729u * (uint32_t)(u & 31) + 243u * (uint32_t)kr;
+                                const uint32_t s = lb & 31;
+                                uint32_t words[9];
 #pragma unroll
-                            for (int j = 0; j < 9; ++j) words[j] = stg[(lb >> 5) + j];
-                            const uint32_t rm = S.tile_mask | ((uint32_t)__ldg(&g_tab.m7[ri]) << 5);
-                            const uint32_t rv = S.tile_val | ((uint32_t)__ldg(&g_tab.v7[ri]) << 5);
+                                for (int j = 0; j < 9; ++j) words[j] = stg[(lb >> 5) + j];
+                                // tile digit 0 = kr, tile digits 1..6 = unit digits
+                                const uint32_t m7 = (kr != 2 ? 1u : 0u) | ((code & 0x3fu) << 1);
+                                const uint32_t v7 = (kr == 1 ? 1u : 0u) | (((code >> 8) & 0x3fu) << 1);
+                                const uint32_t rm = S.tile_mask | (m7 << 5);
+                                const uint32_t rv = S.tile_val | (v7 << 5);
 #pragma unroll
-                            for (int w = 0; w < kChunkWords; ++w) {
-                                uint32_t bits = __funnelshift_r(words[w], words[w + 1], s);
-                                if (w == kChunkWords - 1) bits &= (1u << (243 - 224)) - 1u;
-                                while (bits) {
-                                    const int bb = __ffs(bits) - 1;
-                                    bits &= bits - 1;
-                                    const int q = 32 * w + bb;
-                                    if (k < cap)
-                                        P.pairs[k] = make_uint2((rm | __ldg(&g_tab.t5m[q])) & nmask,
-                                                                (rv | __ldg(&g_tab.t5v[q])) & nmask);
-                                    ++k;
+                                for (int w = 0; w < kChunkWords; ++w) {
+                                    uint32_t bits = __funnelshift_r(words[w], words[w + 1], s);
+                                    if (w == kChunkWords - 1) bits &= (1u << (243 - 224)) - 1u;
+                                    while (bits) {
+                                        const int bb = __ffs(bits) - 1;
+                                        bits &= bits - 1;
+                                        const uint32_t c5 = __ldg(&g_tab.c5[32 * w + bb]);
+                                        if (k < cap)
+                                            P.pairs[k] = make_uint2((rm | (c5 & 0x1fu)) & nmask,
+                                                                    (rv | (c5 >> 8)) & nmask);
+                                        ++k;
+                                    }
                                 }
                             }
                         }
@@ -613,12 +771,9 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 
 // ------------------------------------------------------------------ dispatch
 
-template <int K, int B, int LOAD, int MODE>
-static cudaError_t launch_pass_k(const PassParams &p, uint64_t tiles, cudaStream_t stream)
+template <typename Kern>
+static cudaError_t launch_tiles(Kern kern, size_t smem, const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
-    size_t smem = (size_t)kTileRows * kChunkBytes;
-    if (MODE == kModeOut) smem += (size_t)kTileRows;
-    auto kern = pass_kernel<K, B, LOAD, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (tiles == 0) return cudaSuccess;
@@ -627,16 +782,34 @@ static cudaError_t launch_pass_k(const PassParams &p, uint64_t tiles, cudaStream
     return cudaGetLastError();
 }
 
-template <int LOAD, int MODE>
+// Units of a group digit lie 3^a rows apart in the state.  When that is
+// 1 MB or more, the threads of a warp would each store to another page, so
+// the reduce passes put their rows back in shared memory and store the tile
+// with consecutive lanes on consecutive pieces (STAGE) instead of storing
+// each unit's rows from its thread.
+constexpr uint64_t kStageStrideBytes = 1ull << 20;
+
+template <int K, int B, int LOAD, int MODE, int CM>
+static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t stream)
+{
+    size_t smem = kUnitSmem;
+    if (MODE == kModeOut) smem += (size_t)kTileRows;
+    if constexpr (MODE == kModeMergeReduce || MODE == kModeReduce)
+        if (p.w_g * kChunkBytes >= kStageStrideBytes)
+            return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream);
+    return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, false>, smem, p, tiles, stream);
+}
+
+template <int LOAD, int MODE, int CM>
 static cudaError_t dispatch_group(int K, const PassParams &p, uint64_t tiles, cudaStream_t s)
 {
     switch (K) {
-    case 1: return launch_pass_k<1, 6, LOAD, MODE>(p, tiles, s);
-    case 2: return launch_pass_k<2, 5, LOAD, MODE>(p, tiles, s);
-    case 3: return launch_pass_k<3, 4, LOAD, MODE>(p, tiles, s);
-    case 4: return launch_pass_k<4, 3, LOAD, MODE>(p, tiles, s);
-    case 5: return launch_pass_k<5, 2, LOAD, MODE>(p, tiles, s);
-    case 6: return launch_pass_k<6, 1, LOAD, MODE>(p, tiles, s);
+    case 1: return launch_unit<1, 6, LOAD, MODE, CM>(p, tiles, s);
+    case 2: return launch_unit<2, 5, LOAD, MODE, CM>(p, tiles, s);
+    case 3: return launch_unit<3, 4, LOAD, MODE, CM>(p, tiles, s);
+    case 4: return launch_unit<4, 3, LOAD, MODE, CM>(p, tiles, s);
+    case 5: return launch_unit<5, 2, LOAD, MODE, CM>(p, tiles, s);
+    case 6: return launch_unit<6, 1, LOAD, MODE, CM>(p, tiles, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -675,22 +848,31 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
         const SuperPassDesc &sp = plan.sps[i];
         const PhaseDesc &ph = sp.ph[0];
         a.w_g = pow3(ph.a);
-        a.chunk_mask = ph.chunk_mask;
         a.slot = sp.slot;
         a.fix = sp.sb;
         const uint64_t tiles = sp.n_sb;
         if (ph.load == kLoadTT)
-            e = (ph.K == kTileDigits) ? launch_pass_k<kTileDigits, 0, kLoadTT, kModeMerge>(a, tiles, stream)
-                                      : cudaErrorInvalidValue;
+            e = (ph.K == kTileDigits && ph.a == 0)
+                    ? launch_tiles(tt_pass_kernel, (size_t)kTileRows * kChunkBytes, a, tiles, stream)
+                    : cudaErrorInvalidValue;
+        else if (ph.out && ph.K == kTileDigits && ph.a == 0 && ph.chunk_mask == 0)
+            e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0>(a, tiles, stream);
+        else if (ph.out && ph.K == kTileDigits && ph.a == 0 && ph.chunk_mask == 0x18)
+            e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0x18>(a, tiles, stream);
         else if (ph.out)
-            e = (ph.K == kTileDigits) ? launch_pass_k<kTileDigits, 0, kLoadFull, kModeOut>(a, tiles, stream)
-                                      : cudaErrorInvalidValue;
-        else if (ph.merge && ph.reduce)
-            e = dispatch_group<kLoadSparse, kModeMergeReduce>(ph.K, a, tiles, stream);
-        else if (ph.merge)
-            e = dispatch_group<kLoadSparse, kModeMerge>(ph.K, a, tiles, stream);
+            e = cudaErrorInvalidValue;
+        else if (ph.merge && ph.reduce && ph.chunk_mask == 0x03)
+            e = dispatch_group<kLoadSparse, kModeMergeReduce, 0x03>(ph.K, a, tiles, stream);
+        else if (ph.merge && ph.reduce && ph.chunk_mask == 0x07)
+            e = dispatch_group<kLoadSparse, kModeMergeReduce, 0x07>(ph.K, a, tiles, stream);
+        else if (ph.merge && !ph.reduce && ph.chunk_mask == 0)
+            e = dispatch_group<kLoadSparse, kModeMerge, 0>(ph.K, a, tiles, stream);
+        else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x1c)
+            e = dispatch_group<kLoadFull, kModeReduce, 0x1c>(ph.K, a, tiles, stream);
+        else if (!ph.merge && ph.reduce && ph.chunk_mask == 0)
+            e = dispatch_group<kLoadFull, kModeReduce, 0>(ph.K, a, tiles, stream);
         else
-            e = dispatch_group<kLoadFull, kModeReduce>(ph.K, a, tiles, stream);
+            e = cudaErrorInvalidValue;  // not a pass the plan makes
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
