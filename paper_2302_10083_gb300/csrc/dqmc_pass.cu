@@ -258,8 +258,10 @@ struct PassShared {
     uint64_t base, ttb, tile;
     unsigned long long excl;
     uint32_t warp_tot[kThreads / 32];
-    uint32_t tile_mask, tile_val;
-    int list_ok;
+    uint32_t rcnt[3 * (kThreads / 32)];   // primes per warp region (bitmap pass)
+    uint32_t tile_mask, tile_val;         // literal / value bits of the digits fixed per tile
+    int list_ok, overflow;
+    uint16_t c5[243];                     // copy of the chunk-cell table
     __device__ const FixedDigits &fix() const { return *reinterpret_cast<const FixedDigits *>(fix_raw); }
 };
 
@@ -348,6 +350,69 @@ __global__ void __launch_bounds__(kThreads, 3) tt_pass_kernel(const __grid_const
     }
 }
 
+// List of one bitmap tile read back from the bitmap it has written (its
+// warp regions had more pairs than their slots hold).  Rows 9t .. 9t+8 of the
+// tile belong to thread t < 243.  Every thread of the block calls this.
+__device__ __noinline__ void emit_from_bitmap(const PassParams &P, PassShared &S, uint64_t base)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    auto row_bits = [&](int ri, uint32_t (&bw)[kChunkWords]) {
+        const uint64_t b = (base + (uint64_t)ri) * 243u;
+        const uint64_t wb = b >> 5;
+        const uint32_t sh = (uint32_t)(b & 31);
+        uint32_t wd[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) wd[j] = (wb + j < P.out_words) ? __ldcg(P.out + wb + j) : 0u;
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w) bw[w] = __funnelshift_r(wd[w], wd[w + 1], sh);
+        bw[kChunkWords - 1] &= (1u << (243 - 224)) - 1u;
+    };
+    uint32_t mine = 0;
+    if (tid < 243)
+        for (int r = 0; r < 9; ++r) {
+            uint32_t bw[kChunkWords];
+            row_bits(9 * tid + r, bw);
+#pragma unroll
+            for (int w = 0; w < kChunkWords; ++w) mine += __popc(bw[w]);
+        }
+    uint32_t incl = mine;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) S.warp_tot[wid] = incl;
+    __syncthreads();
+    uint32_t before = incl - mine;
+    for (int w = 0; w < wid; ++w) before += S.warp_tot[w];
+    unsigned long long k = S.excl + before;
+    const uint64_t cap = P.cap;
+    const uint32_t nmask = P.nmask;
+    if (tid < 243 && mine && k < cap) {
+        for (int r = 0; r < 9; ++r) {
+            const int u = 3 * tid + r / 3, kr = r % 3;
+            uint32_t bw[kChunkWords];
+            row_bits(9 * tid + r, bw);
+            const uint32_t code = __ldg(&g_tab.code[u]);
+            const uint32_t m7 = (kr != 2 ? 1u : 0u) | ((code & 0x3fu) << 1);
+            const uint32_t v7 = (kr == 1 ? 1u : 0u) | (((code >> 8) & 0x3fu) << 1);
+            const uint32_t rm = S.tile_mask | (m7 << 5);
+            const uint32_t rv = S.tile_val | (v7 << 5);
+#pragma unroll
+            for (int w = 0; w < kChunkWords; ++w) {
+                uint32_t bits = bw[w];
+                while (bits) {
+                    const int bb = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint32_t c5 = S.c5[32 * w + bb];
+                    if (k < cap) P.pairs[k] = make_uint2((rm | (c5 & 0x1fu)) & nmask, (rv | (c5 >> 8)) & nmask);
+                    ++k;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ unit passes
 //
 // B >= 1: tile row e + 3^B g (inner e < 3^B, group index g < 3^K); unit
@@ -369,6 +434,24 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
     decode_tile<MODE == kModeOut>(P, S);
+    if constexpr (MODE == kModeOut) {
+        for (int i = tid; i < 243; i += kThreads) S.c5[i] = g_tab.c5[i];
+        if (tid == 0) {
+            S.overflow = 0;
+            // literal / value bits of the high digits >= 7 (fixed in this tile)
+            uint64_t xt = S.tile;
+            uint32_t m = 0, vv = 0;
+            for (int d = kTileDigits; d < P.H; ++d) {
+                const uint64_t q = xt / 3u;
+                const uint32_t dg = (uint32_t)(xt - 3u * q);
+                xt = q;
+                if (dg != 2) m |= 1u << (kChunkDigits + d);
+                if (dg == 1) vv |= 1u << (kChunkDigits + d);
+            }
+            S.tile_mask = m;
+            S.tile_val = vv;
+        }
+    }
     const uint64_t base = S.base;
     const uint64_t w_g = P.w_g;
     uint4 *const state = P.state;
@@ -448,7 +531,6 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         const uint32_t o = (uint32_t)(bit0 & 31);
         const uint64_t W0 = bit0 >> 5;
         const bool last_tile = (base + kTileRows == P.total_rows);
-        uint8_t *const cnt = reinterpret_cast<uint8_t *>(tile + kZeroSlot + 6);  // primes per row (out)
 
         // A unit is read only by units of smaller or equal index (its '*'
         // neighbours lie above it), so once a round's reads of a row are
@@ -540,50 +622,67 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
 #pragma unroll
                         for (int w = 0; w < kChunkWords; ++w) x[k][w] = 0u;
                 }
-                // ------------------------------------- count and dense bits
+                // ---------------------------- count, dense bits, list pairs
+                uint32_t c3 = 0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    uint32_t c = 0;
+                for (int k = 0; k < 3; ++k)
 #pragma unroll
-                    for (int w = 0; w < kChunkWords; ++w) c += __popc(x[k][w]);
-                    my_count += c;
-                    if (u < kUnits) cnt[3 * u + k] = (uint8_t)c;  // <= 243
+                    for (int w = 0; w < kChunkWords; ++w) c3 += __popc(x[k][w]);
+                my_count += c3;
+                // this unit's first pair among its warp's (warp scan)
+                uint32_t incl = c3;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += y;
                 }
-                // every read of this round's units is done: each warp stages
-                // the dense bits of its 32 units in their slots and keeps them
-                // for the list
+                const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                if (lane == 0) S.rcnt[rd * (kThreads / 32) + wid] = wtot;
+                // every read of this round's units is done: each warp writes
+                // the dense bits of its 32 units into their slots, stores
+                // them to the bitmap, then keeps its units' pairs there
                 __syncthreads();
                 const int U0 = rd * kThreads + wid * 32;
                 const int nun = min(32, kUnits - U0);
                 if (nun > 0) {
                     uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 6 * U0);
                     // these units are tile bits 729*U0 ..: words S0 .. of the
-                    // bitmap, starting at bit o of word S0
-                    const uint32_t hi_bit = o + 729u * (uint32_t)nun;   // end of these units' bits
-                    const int nw4 = (int)((hi_bit + 127u) >> 7);        // uint4 words holding them
-                    for (int i = lane; i < nw4; i += 32) reinterpret_cast<uint4 *>(stg)[i] = make_uint4(0u, 0u, 0u, 0u);
-                    __syncwarp();
-                    if (u < kUnits) {
+                    // bitmap, starting at bit o of word S0.  Unit 'lane' starts
+                    // at bit lb0 of stg; its rows follow each other.  A word
+                    // shared by two rows of the unit is carried in a register,
+                    // one shared with the next unit goes to the next lane.
+                    const uint32_t lb0 = o + 729u * (uint32_t)lane;
+                    const uint32_t s0 = lb0 & 31;
+                    uint32_t *const uw = stg + (lb0 >> 5);
+                    uint32_t carry = 0, first = 0;
+                    if (valid) {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
-                            const uint32_t lb = o + 729u * (uint32_t)lane + 243u * (uint32_t)k;
-                            const uint32_t k0 = lb >> 5, s = lb & 31;
-                            const uint32_t cw = (s + 243u + 31u) >> 5;  // 8 or 9 words
+                            const uint32_t sb = s0 + 243u * (uint32_t)k;  // row k's first bit, from uw
+                            const uint32_t sh = sb & 31;
+                            uint32_t *const rw = uw + (sb >> 5);
                             uint32_t w9[9];
-                            w9[0] = x[k][0] << s;
+                            w9[0] = (x[k][0] << sh) | carry;
 #pragma unroll
-                            for (int j = 1; j < 8; ++j) w9[j] = __funnelshift_l(x[k][j - 1], x[k][j], s);
-                            w9[8] = __funnelshift_l(x[k][7], 0u, s);
-                            atomicOr(&stg[k0], w9[0]);
+                            for (int j = 1; j < 8; ++j) w9[j] = __funnelshift_l(x[k][j - 1], x[k][j], sh);
+                            w9[8] = __funnelshift_l(x[k][7], 0u, sh);
+                            // the row ends in word 8 (sh >= 13) or word 7
+                            const bool nine = sh >= 13u;
+                            if (k == 0) first = w9[0];
+                            else rw[0] = w9[0];
 #pragma unroll
-                            for (int j = 1; j < 8; ++j) {
-                                if ((uint32_t)j < cw - 1) stg[k0 + j] = w9[j];
-                                else if ((uint32_t)j == cw - 1) atomicOr(&stg[k0 + j], w9[j]);
-                            }
-                            if (cw == 9) atomicOr(&stg[k0 + 8], w9[8]);
+                            for (int j = 1; j < 7; ++j) rw[j] = w9[j];
+                            if (nine) rw[7] = w9[7];
+                            carry = nine ? w9[8] : w9[7];
                         }
                     }
+                    const uint32_t cin = __shfl_up_sync(0xffffffffu, carry, 1);
+                    if (valid) {
+                        uw[0] = first | (lane > 0 ? cin : 0u);
+                        if (lane == nun - 1) uw[(s0 + 729u) >> 5] = carry;  // the region's last word
+                    }
                     __syncwarp();
+                    const uint32_t hi_bit = o + 729u * (uint32_t)nun;   // end of these units' bits
                     const uint64_t S0 = W0 + (uint64_t)729 * (uint64_t)(U0 >> 5);
                     if (nun == 32 && ck(P, S0 + 730 <= P.out_alloc_words, S0 + 730)) {
                         // 32 full units: words 1 .. 728 hold only their bits;
@@ -623,6 +722,38 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                                 atomicAnd(dst, val | ~m);
                                 atomicOr(dst, val & m);
                             }
+                        }
+                    }
+                    __syncwarp();
+                    // (mask, value) pairs of these units, in rho order, in the
+                    // slots just freed; copied to the list after the look-back
+                    if (P.pairs) {
+                        if (wtot <= 12u * (uint32_t)nun) {   // a unit's 96 bytes hold 12 pairs
+                            if (valid && c3) {
+                                uint2 *pr = reinterpret_cast<uint2 *>(stg) + (incl - c3);
+                                const uint32_t code = __ldg(&g_tab.code[u]);
+                                const uint32_t nmask = P.nmask;
+#pragma unroll
+                                for (int k = 0; k < 3; ++k) {
+                                    // tile digit 0 = k, tile digits 1..6 = unit digits
+                                    const uint32_t m7 = (k != 2 ? 1u : 0u) | ((code & 0x3fu) << 1);
+                                    const uint32_t v7 = (k == 1 ? 1u : 0u) | (((code >> 8) & 0x3fu) << 1);
+                                    const uint32_t rm = S.tile_mask | (m7 << 5);
+                                    const uint32_t rv = S.tile_val | (v7 << 5);
+#pragma unroll
+                                    for (int w = 0; w < kChunkWords; ++w) {
+                                        uint32_t bits = x[k][w];
+                                        while (bits) {
+                                            const int bb = __ffs(bits) - 1;
+                                            bits &= bits - 1;
+                                            const uint32_t c5 = S.c5[32 * w + bb];
+                                            *pr++ = make_uint2((rm | (c5 & 0x1fu)) & nmask, (rv | (c5 >> 8)) & nmask);
+                                        }
+                                    }
+                                }
+                            }
+                        } else if (lane == 0) {
+                            S.overflow = 1;
                         }
                     }
                 }
@@ -667,74 +798,27 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                     if (lane == 0) {
                         S.excl = ex;
                         S.list_ok = ok;
-                        // mask / value bits of the high digits >= 7 (fixed in this tile)
-                        uint64_t xt = T;
-                        uint32_t m = 0, vv = 0;
-                        for (int d = kTileDigits; d < P.H; ++d) {
-                            const uint64_t q = xt / 3u;
-                            const uint32_t dg = (uint32_t)(xt - 3u * q);
-                            xt = q;
-                            if (dg != 2) m |= 1u << (5 + d);
-                            if (dg == 1) vv |= 1u << (5 + d);
-                        }
-                        S.tile_mask = m;
-                        S.tile_val = vv;
                     }
                 }
                 __syncthreads();
-                if (S.list_ok) {
-                    // units 3t .. 3t+2 (rows 9t .. 9t+8) belong to thread t < 243
-                    uint32_t mine = 0;
-                    if (tid < 243)
-                        for (int r = 0; r < 9; ++r) mine += cnt[9 * tid + r];
-                    uint32_t incl = mine;
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
-                        if (lane >= off) incl += y;
+                const uint64_t cap = P.cap;
+                if (S.list_ok && !S.overflow) {
+                    // each region's pairs to the list, region r = units 32r ..
+                    constexpr int kRegions = (kUnits + 31) / 32;
+                    for (int r = wid; r < kRegions; r += kThreads / 32) {
+                        uint32_t off = 0;
+                        for (int q = 0; q < r; ++q) off += S.rcnt[q];
+                        const uint32_t nr = S.rcnt[r];
+                        const uint2 *src = reinterpret_cast<const uint2 *>(tile + 6 * 32 * r);
+                        const unsigned long long k0 = S.excl + off;
+                        for (uint32_t i = lane; i < nr; i += 32)
+                            if (k0 + i < cap) P.pairs[k0 + i] = src[i];
                     }
-                    __syncthreads();
-                    if (lane == 31) S.warp_tot[wid] = incl;
-                    __syncthreads();
-                    uint32_t before = incl - mine;
-                    for (int w = 0; w < wid; ++w) before += S.warp_tot[w];
-                    unsigned long long k = S.excl + before;
-                    const uint64_t cap = P.cap;
-                    const uint32_t nmask = P.nmask;
-                    if (tid < 243 && mine && k < cap) {
-                        for (int uu = 0; uu < 3; ++uu) {
-                            const int u = 3 * tid + uu;
-                            const uint32_t code = __ldg(&g_tab.code[u]);
-                            // this unit's bits, staged in its warp's slots
-                            const uint32_t *const stg = reinterpret_cast<const uint32_t *>(tile + 6 * (u & ~31));
-                            for (int kr = 0; kr < 3; ++kr) {
-                                if (!cnt[3 * u + kr]) continue;
-                                const uint32_t lb = o + 729u * (uint32_t)(u & 31) + 243u * (uint32_t)kr;
-                                const uint32_t s = lb & 31;
-                                uint32_t words[9];
-#pragma unroll
-                                for (int j = 0; j < 9; ++j) words[j] = stg[(lb >> 5) + j];
-                                // tile digit 0 = kr, tile digits 1..6 = unit digits
-                                const uint32_t m7 = (kr != 2 ? 1u : 0u) | ((code & 0x3fu) << 1);
-                                const uint32_t v7 = (kr == 1 ? 1u : 0u) | (((code >> 8) & 0x3fu) << 1);
-                                const uint32_t rm = S.tile_mask | (m7 << 5);
-                                const uint32_t rv = S.tile_val | (v7 << 5);
-#pragma unroll
-                                for (int w = 0; w < kChunkWords; ++w) {
-                                    uint32_t bits = __funnelshift_r(words[w], words[w + 1], s);
-                                    if (w == kChunkWords - 1) bits &= (1u << (243 - 224)) - 1u;
-                                    while (bits) {
-                                        const int bb = __ffs(bits) - 1;
-                                        bits &= bits - 1;
-                                        const uint32_t c5 = __ldg(&g_tab.c5[32 * w + bb]);
-                                        if (k < cap)
-                                            P.pairs[k] = make_uint2((rm | (c5 & 0x1fu)) & nmask,
-                                                                    (rv | (c5 >> 8)) & nmask);
-                                        ++k;
-                                    }
-                                }
-                            }
-                        }
-                    }
+                } else if (S.list_ok) {
+                    // a region had more pairs than its slots hold: list this
+                    // tile from the bitmap it has written (rows 9t .. 9t+8
+                    // belong to thread t < 243)
+                    emit_from_bitmap(P, S, base);
                 }
             }
         }
@@ -793,7 +877,6 @@ template <int K, int B, int LOAD, int MODE, int CM>
 static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
     size_t smem = kUnitSmem;
-    if (MODE == kModeOut) smem += (size_t)kTileRows;
     if constexpr (MODE == kModeMergeReduce || MODE == kModeReduce)
         if (p.w_g * kChunkBytes >= kStageStrideBytes)
             return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream);

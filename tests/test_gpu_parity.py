@@ -65,6 +65,39 @@ def test_multipass(n):
         check_all(n, on, dc)
 
 
+def _embedded_band(n, k, lo, hi):
+    """f(x) = [lo <= weight(x_0 .. x_{k-1}) <= hi] when x_k .. x_{n-1} are all
+    0, else 0: C(k, lo) * C(k - lo, k - hi) primes, all in the first 3^(k-5)
+    rows."""
+    x = np.arange(1 << k)
+    w = np.zeros(x.size, dtype=np.int64)
+    for i in range(k):
+        w += (x >> i) & 1
+    h = np.packbits(((w >= lo) & (w <= hi)).astype(np.uint8), bitorder="little")
+    on = np.zeros(synth.tt_bytes(n), dtype=np.uint8)
+    on[: h.size] = h
+    return on
+
+
+@pytest.mark.parametrize("n", [13, 16])
+def test_dense_primes_in_few_rows(n):
+    """More primes in 96 rows of the first bitmap tile than their shared-memory
+    slots hold (12 pairs per three-row unit): the bitmap pass lists that tile
+    from the bitmap it wrote instead."""
+    on = _embedded_band(n, 10, 3, 6)
+    S = oracle.sweep(n, on)
+    rows = oracle.pairs(n, S)
+    assert len(rows) == 120 * 35   # C(10, 3) * C(7, 4)
+    rho = np.zeros(len(rows), dtype=np.int64)
+    for i in range(n):   # rho of each listed cube from its (mask, value) pair
+        lit = (rows[:, 0] >> i) & 1
+        one = (rows[:, 1] >> i) & 1
+        rho += np.where(lit == 1, one, 2).astype(np.int64) * 3 ** i
+    per_region = np.bincount(rho // 243 // 96)
+    assert per_region.max() > 12 * 32
+    check_all(n, on)
+
+
 @pytest.mark.parametrize("n", [18, 19])
 def test_multipass_larger(n):
     on, dc = synth.random_function(n, 5, 0.9, 0.05)
