@@ -262,6 +262,7 @@ struct PassShared {
     uint32_t tile_mask, tile_val;         // literal / value bits of the digits fixed per tile
     int list_ok, overflow;
     uint16_t c5[243];                     // copy of the chunk-cell table
+    uint16_t code[kUnits];                // copy of the unit-digit table
     __device__ const FixedDigits &fix() const { return *reinterpret_cast<const FixedDigits *>(fix_raw); }
 };
 
@@ -434,6 +435,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
     decode_tile<MODE == kModeOut>(P, S);
+    for (int i = tid; i < kUnits; i += kThreads) S.code[i] = g_tab.code[i];
     if constexpr (MODE == kModeOut) {
         for (int i = tid; i < 243; i += kThreads) S.c5[i] = g_tab.c5[i];
         if (tid == 0) {
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         constexpr uint32_t gmask = (0x3fu >> D0) << D0;
         for (int p = tid; p < kUnits * 6; p += kThreads) {
             const int u = p / 6, c = p - 6 * u;
-            if (!(~(uint32_t)__ldg(&g_tab.code[u]) & gmask)) continue;
+            if (!(~(uint32_t)S.code[u] & gmask)) continue;
             const uint64_t row0 = unit_row(u);
             if (!ck(P, row0 + 2 < state_rows, row0 + 2)) continue;
             state[2 * row0 + c] = tile[uslot(u, c)];
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             // se: even pieces (first row halves), so: odd pieces.
             int se[6 - D0], so[6 - D0];
             {
-                const uint32_t code = valid ? (uint32_t)__ldg(&g_tab.code[u]) : 0u;
+                const uint32_t code = valid ? (uint32_t)S.code[u] : 0u;
                 static_for<D0, 6>([&](auto Dg) {
                     constexpr int d = decltype(Dg)::value;
                     constexpr int Dd = (int)pow3(d);
@@ -583,8 +585,9 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                 for (int w = 0; w < kChunkWords; ++w) xr[w] &= ~acc[w];
             };
 
-            if constexpr (MODE != kModeOut && STAGE) {
-                // Row k of a unit is read only while rows k are reduced: the
+            if constexpr (STAGE || MODE == kModeOut) {
+                // Row k of a unit is read only while rows k are reduced (and,
+                // in the bitmap pass, row 2 by its own unit before that): the
                 // reduced row goes back to its slot after this round's reads.
 #pragma unroll 1
                 for (int k = 0; k < 3; ++k) {
@@ -611,25 +614,40 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                         }
                     }
                 }
-            } else {
+            }
+        }
+
+        if constexpr (MODE == kModeOut) {
+            // ------------------------------------------------ bitmap and list
+            // The tile now holds the reduced rows.  Region r = units 32r ..
+            // belongs to one warp: count, dense bits into the region's own
+            // slots, bitmap store, then the region's pairs in those slots.
+            __syncthreads();
+            constexpr int kRegions = (kUnits + 31) / 32;
+            for (int r = wid; r < kRegions; r += kThreads / 32) {
+                const int U0 = 32 * r;
+                const int nun = min(32, kUnits - U0);
+                const int u = U0 + lane;
+                const bool valid = lane < nun;
                 uint32_t x[3][kChunkWords];
-                if (valid) {
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) finish_row(k, x[k]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
+                for (int k = 0; k < 3; ++k) {
+                    if (valid) {
+                        const uint4 q0 = tile[uslot(u, 2 * k)], q1 = tile[uslot(u, 2 * k + 1)];
+                        x[k][0] = q0.x; x[k][1] = q0.y; x[k][2] = q0.z; x[k][3] = q0.w;
+                        x[k][4] = q1.x; x[k][5] = q1.y; x[k][6] = q1.z; x[k][7] = q1.w;
+                    } else {
 #pragma unroll
                         for (int w = 0; w < kChunkWords; ++w) x[k][w] = 0u;
+                    }
                 }
-                // ---------------------------- count, dense bits, list pairs
                 uint32_t c3 = 0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) c3 += __popc(x[k][w]);
                 my_count += c3;
-                // this unit's first pair among its warp's (warp scan)
+                // this unit's first pair among the region's (warp scan)
                 uint32_t incl = c3;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
@@ -637,14 +655,9 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                     if (lane >= off) incl += y;
                 }
                 const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-                if (lane == 0) S.rcnt[rd * (kThreads / 32) + wid] = wtot;
-                // every read of this round's units is done: each warp writes
-                // the dense bits of its 32 units into their slots, stores
-                // them to the bitmap, then keeps its units' pairs there
-                __syncthreads();
-                const int U0 = rd * kThreads + wid * 32;
-                const int nun = min(32, kUnits - U0);
-                if (nun > 0) {
+                if (lane == 0) S.rcnt[r] = wtot;
+                __syncwarp();   // every lane holds its rows: the region's slots are free
+                {
                     uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 6 * U0);
                     // these units are tile bits 729*U0 ..: words S0 .. of the
                     // bitmap, starting at bit o of word S0.  Unit 'lane' starts
@@ -731,15 +744,18 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                         if (wtot <= 12u * (uint32_t)nun) {   // a unit's 96 bytes hold 12 pairs
                             if (valid && c3) {
                                 uint2 *pr = reinterpret_cast<uint2 *>(stg) + (incl - c3);
-                                const uint32_t code = __ldg(&g_tab.code[u]);
+                                const uint32_t code = S.code[u];
                                 const uint32_t nmask = P.nmask;
+                                // cube bits: tile digits 1..6 are the unit digits
+                                const uint32_t um = S.tile_mask | ((code & 0x3fu) << (kChunkDigits + 1));
+                                const uint32_t uv = S.tile_val | (((code >> 8) & 0x3fu) << (kChunkDigits + 1));
+                                // lanes walk their own row words; a word's
+                                // bits come out in rho order
 #pragma unroll
                                 for (int k = 0; k < 3; ++k) {
-                                    // tile digit 0 = k, tile digits 1..6 = unit digits
-                                    const uint32_t m7 = (k != 2 ? 1u : 0u) | ((code & 0x3fu) << 1);
-                                    const uint32_t v7 = (k == 1 ? 1u : 0u) | (((code >> 8) & 0x3fu) << 1);
-                                    const uint32_t rm = S.tile_mask | (m7 << 5);
-                                    const uint32_t rv = S.tile_val | (v7 << 5);
+                                    // tile digit 0 = k
+                                    const uint32_t rm = um | (k != 2 ? 1u << kChunkDigits : 0u);
+                                    const uint32_t rv = uv | (k == 1 ? 1u << kChunkDigits : 0u);
 #pragma unroll
                                     for (int w = 0; w < kChunkWords; ++w) {
                                         uint32_t bits = x[k][w];
@@ -805,10 +821,16 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                 if (S.list_ok && !S.overflow) {
                     // each region's pairs to the list, region r = units 32r ..
                     constexpr int kRegions = (kUnits + 31) / 32;
+                    static_assert(kRegions <= 32, "one lane per region");
+                    const uint32_t rc = (lane < kRegions) ? S.rcnt[lane] : 0u;
+                    uint32_t ri = rc;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, ri, off);
+                        if (lane >= off) ri += y;
+                    }
                     for (int r = wid; r < kRegions; r += kThreads / 32) {
-                        uint32_t off = 0;
-                        for (int q = 0; q < r; ++q) off += S.rcnt[q];
-                        const uint32_t nr = S.rcnt[r];
+                        const uint32_t nr = __shfl_sync(0xffffffffu, rc, r);
+                        const uint32_t off = __shfl_sync(0xffffffffu, ri, r) - nr;
                         const uint2 *src = reinterpret_cast<const uint2 *>(tile + 6 * 32 * r);
                         const unsigned long long k0 = S.excl + off;
                         for (uint32_t i = lane; i < nr; i += 32)
