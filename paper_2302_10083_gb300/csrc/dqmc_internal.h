@@ -101,6 +101,7 @@ constexpr int kTileRows = 2187;     // 3^7
 
 Plan make_plan(int n);
 std::string describe_plan(const Plan &p);
+int plan_passes(const Plan &p);     // kernel launches of the sweep
 
 // Workspace layout (offsets in bytes from the workspace base, 256-aligned).
 struct Workspace {
@@ -117,12 +118,28 @@ Workspace workspace_layout(int n);
 uint64_t bitmap_words(int n);        // ceil(3^n / 32)
 uint64_t bitmap_alloc_bytes(int n);  // ceil(3^n / 8) rounded up to 16
 
+// A batch of functions with the same n (device tables, indexed by function
+// id): the pass kernels and the one-tile kernel run every function of the
+// batch in one launch per pass.  Counts are not zeroed by the launches.
+struct BatchArgs {
+    const uint32_t *fn = nullptr;          // ids of the batch's functions
+    uint32_t nfun = 0;
+    const uint64_t *tt_off = nullptr;      // byte offset of the ON table in arena
+    const uint64_t *dc_off = nullptr;      // byte offset of the DC table, ~0: none
+    const uint64_t *bm_off = nullptr;      // byte offset of the bitmap in bitmaps
+    const uint8_t *arena = nullptr;
+    uint8_t *bitmaps = nullptr;
+    unsigned long long *count = nullptr;   // one per function id
+};
+
 // Enqueue the whole sweep.  d_count must point to a uint64 (zeroed here).
 // Passes [first, last) only (0 .. passes.size() for the whole sweep); pass 0
-// zeroes *d_count first.
+// zeroes *d_count first.  With a batch (n <= 12), one CTA per function and
+// d_on / d_dc / d_bitmap / d_count are unused.
 cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc,
                          void *d_state, uint32_t *d_bitmap, unsigned long long *d_count,
-                         cudaStream_t stream, int first = 0, int last = -1);
+                         cudaStream_t stream, int first = 0, int last = -1,
+                         const BatchArgs *batch = nullptr);
 
 // Bytes pass i moves by design (rows read and written x 32, truth tables, bitmap).
 uint64_t pass_bytes(const Plan &plan, int i, bool with_dc);
@@ -145,10 +162,13 @@ constexpr uint32_t kErrTimeout = 0x54494d45u;  // "TIME"
 constexpr uint32_t kErrBounds = 0x424f554eu;   // "BOUN"
 
 // Enqueue passes [first, last) of a plan (n >= 13, dqmc_pass.cu).  d_pairs
-// may be null (no list).
+// may be null (no list).  With a batch, d_state holds one state per batch
+// function (state_rows rows each), d_on / d_dc / d_bitmap / d_count / d_pairs
+// are unused and no list is written.
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
                          uint32_t *d_bitmap, unsigned long long *d_count, uint32_t *d_pairs,
-                         uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last);
+                         uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last,
+                         const BatchArgs *batch = nullptr);
 
 // Test hook: a device wait on a counter nothing sets; it must time out.
 cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wait_ns, cudaStream_t stream);

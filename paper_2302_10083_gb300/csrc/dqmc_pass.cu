@@ -115,7 +115,44 @@ struct PassParams {
     uint32_t nmask;             // (1 << n) - 1
     int H, slot;
     FixedDigits fix;            // digits fixed per tile, ascending
+    // Batch mode (bfn non-null): block b works on tile b % tiles_per_fn of
+    // function bfn[b / tiles_per_fn]; its truth tables, bitmap and count come
+    // from the batch tables, its state is state + (b / tiles_per_fn) *
+    // bstate_stride, and on / dc / out / count above are unused.
+    const uint32_t *bfn;
+    const uint64_t *btt_off, *bdc_off, *bbm_off;   // byte offsets; bdc_off ~0: no don't-cares
+    const uint8_t *barena;
+    uint8_t *bbitmaps;
+    unsigned long long *bcount;
+    uint64_t bstate_stride;     // uint4 per function
+    uint32_t tiles_per_fn;
 };
+
+// The function a block works on: its buffers and its tile index.
+struct FnBufs {
+    const uint32_t *on, *dc;
+    uint4 *state;
+    uint32_t *out;
+    unsigned long long *count;
+    uint64_t tile;
+};
+
+__device__ __forceinline__ FnBufs fn_bufs(const PassParams &P)
+{
+    FnBufs f{P.on, P.dc, P.state, P.out, P.count, blockIdx.x};
+    if (P.bfn) {
+        const uint32_t fi = blockIdx.x / P.tiles_per_fn;
+        f.tile = blockIdx.x - (uint64_t)fi * P.tiles_per_fn;
+        const uint32_t id = P.bfn[fi];
+        f.on = reinterpret_cast<const uint32_t *>(P.barena + P.btt_off[id]);
+        const uint64_t dco = P.bdc_off[id];
+        f.dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(P.barena + dco);
+        f.state = P.state + (uint64_t)fi * P.bstate_stride;
+        f.out = reinterpret_cast<uint32_t *>(P.bbitmaps + P.bbm_off[id]);
+        f.count = P.bcount + id;
+    }
+    return f;
+}
 
 constexpr int kThreads = 256;
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
@@ -270,7 +307,7 @@ struct PassShared {
 // With kTicket and a list, tiles take ids in the order they start, so a
 // tile's look-back waits only on tiles already running.
 template <bool kTicket>
-__device__ __forceinline__ void decode_tile(const PassParams &P, PassShared &S)
+__device__ __forceinline__ void decode_tile(const PassParams &P, PassShared &S, uint64_t tile)
 {
     const int tid = threadIdx.x;
     {
@@ -281,7 +318,7 @@ __device__ __forceinline__ void decode_tile(const PassParams &P, PassShared &S)
     __syncthreads();
     if (tid == 0) {
         const FixedDigits &f = S.fix();
-        uint64_t t = blockIdx.x;
+        uint64_t t = tile;
         if (kTicket && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
         uint64_t base = 0, ttb = 0, x = t;
         for (int i = 0; i < f.n; ++i) {
@@ -313,13 +350,14 @@ __global__ void __launch_bounds__(kThreads, 3) tt_pass_kernel(const __grid_const
     extern __shared__ uint4 tile[];
     __shared__ PassShared S;
     const int tid = threadIdx.x;
-    decode_tile<false>(P, S);
+    const FnBufs F = fn_bufs(P);
+    decode_tile<false>(P, S, F.tile);
     const uint64_t base = S.base, ttb = S.ttb;
 
     for (int gb = tid; gb < (1 << kTileDigits); gb += kThreads) {
         if (!ck(P, ttb + gb < P.tt_words, ttb + gb)) continue;
-        uint32_t x = __ldg(P.on + ttb + gb);
-        if (P.dc) x |= __ldg(P.dc + ttb + gb);
+        uint32_t x = __ldg(F.on + ttb + gb);
+        if (F.dc) x |= __ldg(F.dc + ttb + gb);
         uint32_t v[kChunkWords];
         chunk_from_word_p(x, v);
         const int r = __ldg(&g_tab.sp3[gb]);
@@ -347,14 +385,14 @@ __global__ void __launch_bounds__(kThreads, 3) tt_pass_kernel(const __grid_const
         const int h = pc & 1, ri = pc >> 1;
         const uint64_t row = base + ri;
         if (!ck(P, row < P.state_rows, row)) continue;
-        P.state[2 * row + h] = tile[slotp(ri, h)];
+        F.state[2 * row + h] = tile[slotp(ri, h)];
     }
 }
 
 // List of one bitmap tile read back from the bitmap it has written (its
 // warp regions had more pairs than their slots hold).  Rows 9t .. 9t+8 of the
 // tile belong to thread t < 243.  Every thread of the block calls this.
-__device__ __noinline__ void emit_from_bitmap(const PassParams &P, PassShared &S, uint64_t base)
+__device__ __noinline__ void emit_from_bitmap(const PassParams &P, PassShared &S, const uint32_t *out, uint64_t base)
 {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     auto row_bits = [&](int ri, uint32_t (&bw)[kChunkWords]) {
@@ -363,7 +401,7 @@ __device__ __noinline__ void emit_from_bitmap(const PassParams &P, PassShared &S
         const uint32_t sh = (uint32_t)(b & 31);
         uint32_t wd[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) wd[j] = (wb + j < P.out_words) ? __ldcg(P.out + wb + j) : 0u;
+        for (int j = 0; j < 9; ++j) wd[j] = (wb + j < P.out_words) ? __ldcg(out + wb + j) : 0u;
 #pragma unroll
         for (int w = 0; w < kChunkWords; ++w) bw[w] = __funnelshift_r(wd[w], wd[w + 1], sh);
         bw[kChunkWords - 1] &= (1u << (243 - 224)) - 1u;
@@ -434,7 +472,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
     __shared__ PassShared S;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
-    decode_tile<MODE == kModeOut>(P, S);
+    const FnBufs F = fn_bufs(P);
+    decode_tile<MODE == kModeOut>(P, S, F.tile);
     for (int i = tid; i < kUnits; i += kThreads) S.code[i] = g_tab.code[i];
     if constexpr (MODE == kModeOut) {
         for (int i = tid; i < 243; i += kThreads) S.c5[i] = g_tab.c5[i];
@@ -456,7 +495,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
     }
     const uint64_t base = S.base;
     const uint64_t w_g = P.w_g;
-    uint4 *const state = P.state;
+    uint4 *const state = F.state;
+    uint32_t *const out = F.out;
     const uint64_t state_rows = P.state_rows;
     // first state row of unit u
     auto unit_row = [&](int u) -> uint64_t {
@@ -700,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                     if (nun == 32 && ck(P, S0 + 730 <= P.out_alloc_words, S0 + 730)) {
                         // 32 full units: words 1 .. 728 hold only their bits;
                         // word 0 holds them from bit o up, word 729 below bit o.
-                        uint32_t *const dstw = P.out + S0;
+                        uint32_t *const dstw = out + S0;
 #pragma unroll 4
                         for (int j = 1 + lane; j <= 728; j += 32) dstw[j] = stg[j];
                         if (lane == 0) {
@@ -727,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                             if (hi2 <= lo) continue;
                             if (!ck(P, wi < P.out_alloc_words, wi)) continue;
                             const uint32_t val = stg[j];
-                            uint32_t *dst = P.out + wi;
+                            uint32_t *dst = out + wi;
                             if (lo == 0 && hi2 == 32) {
                                 *dst = val;
                             } else {
@@ -788,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             }
         } else if constexpr (MODE == kModeOut) {
             if (last_tile)
-                for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += kThreads) P.out[w] = 0u;
+                for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += kThreads) out[w] = 0u;
             // tile count
             uint32_t xs = my_count;
             for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
@@ -797,7 +837,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             uint32_t tile_total = 0;
 #pragma unroll
             for (int w = 0; w < kThreads / 32; ++w) tile_total += S.warp_tot[w];
-            if (tid == 0 && tile_total) atomicAdd(P.count, (unsigned long long)tile_total);
+            if (tid == 0 && tile_total) atomicAdd(F.count, (unsigned long long)tile_total);
             if (P.pairs) {
                 const uint64_t T = S.tile;
                 if (wid == 0) {
@@ -840,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                     // a region had more pairs than its slots hold: list this
                     // tile from the bitmap it has written (rows 9t .. 9t+8
                     // belong to thread t < 243)
-                    emit_from_bitmap(P, S, base);
+                    emit_from_bitmap(P, S, out, base);
                 }
             }
         }
@@ -921,12 +961,17 @@ static cudaError_t dispatch_group(int K, const PassParams &p, uint64_t tiles, cu
 
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state, uint32_t *d_bitmap,
                          unsigned long long *d_count, uint32_t *d_pairs, uint64_t cap, void *d_ctrl,
-                         cudaStream_t stream, int first, int last)
+                         cudaStream_t stream, int first, int last, const BatchArgs *batch)
 {
     const CtrlLayout cl = ctrl_layout(plan);
     cudaError_t e = cudaSuccess;
+    if (batch) {
+        if (batch->nfun == 0) return cudaSuccess;
+        d_pairs = nullptr;
+        cap = 0;
+    }
     if (first == 0) {
-        e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream);
+        if (!batch) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_ctrl, 0, cl.bytes, stream);
         if (e != cudaSuccess) return e;
     }
@@ -949,13 +994,24 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
     a.wait_ns = 1000000000ull;
     a.nmask = (uint32_t)((1ull << plan.n) - 1);
     a.H = plan.H;
+    if (batch) {
+        a.bfn = batch->fn;
+        a.btt_off = batch->tt_off;
+        a.bdc_off = batch->dc_off;
+        a.bbm_off = batch->bm_off;
+        a.barena = batch->arena;
+        a.bbitmaps = batch->bitmaps;
+        a.bcount = batch->count;
+        a.bstate_stride = 2 * plan.state_rows;
+    }
     for (int i = first; i < last; ++i) {
         const SuperPassDesc &sp = plan.sps[i];
         const PhaseDesc &ph = sp.ph[0];
         a.w_g = pow3(ph.a);
         a.slot = sp.slot;
         a.fix = sp.sb;
-        const uint64_t tiles = sp.n_sb;
+        a.tiles_per_fn = (uint32_t)sp.n_sb;
+        const uint64_t tiles = sp.n_sb * (batch ? batch->nfun : 1u);
         if (ph.load == kLoadTT)
             e = (ph.K == kTileDigits && ph.a == 0)
                     ? launch_tiles(tt_pass_kernel, (size_t)kTileRows * kChunkBytes, a, tiles, stream)

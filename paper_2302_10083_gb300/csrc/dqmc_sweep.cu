@@ -46,6 +46,13 @@ struct PassArgs {
     uint64_t out_words;         // ceil(3^n / 32)
     uint64_t out_alloc_words;   // bitmap allocation in words (16-byte multiple)
     int top_binary, fuse_reduce, chunk_reduce, write_out;
+    // Batch mode (bfn non-null, one tile per function): block b works on
+    // function bfn[b]; on / dc / out / count come from the batch tables.
+    const uint32_t *bfn;
+    const uint64_t *btt_off, *bdc_off, *bbm_off;   // byte offsets; bdc_off ~0: no don't-cares
+    const uint8_t *barena;
+    uint8_t *bbitmaps;
+    unsigned long long *bcount;
 };
 
 __device__ __forceinline__ uint64_t spread3(uint64_t x)
@@ -181,7 +188,19 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
     extern __shared__ uint4 smem[];
     __shared__ uint16_t sp3[NB];
 
-    const uint64_t tile = blockIdx.x;
+    const uint32_t *p_on = p.on, *p_dc = p.dc;
+    uint32_t *p_out = p.out;
+    unsigned long long *p_count = p.count;
+    uint64_t tile = blockIdx.x;
+    if (p.bfn) {
+        const uint32_t id = p.bfn[blockIdx.x];
+        tile = 0;
+        p_on = reinterpret_cast<const uint32_t *>(p.barena + p.btt_off[id]);
+        const uint64_t dco = p.bdc_off[id];
+        p_dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(p.barena + dco);
+        p_out = reinterpret_cast<uint32_t *>(p.bbitmaps + p.bbm_off[id]);
+        p_count = p.bcount + id;
+    }
     const uint64_t mid = tile % p.n_mid;
     const uint64_t topi = tile / p.n_mid;
     const uint64_t top_t = p.top_binary ? spread3(topi) : topi;
@@ -197,11 +216,11 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
             uint32_t x;
             if constexpr (C == kChunkDigits) {
                 const uint64_t wi = topi * NB + gb;
-                x = __ldg(p.on + wi);
-                if (p.dc) x |= __ldg(p.dc + wi);
+                x = __ldg(p_on + wi);
+                if (p_dc) x |= __ldg(p_dc + wi);
             } else {
-                const uint8_t *on8 = reinterpret_cast<const uint8_t *>(p.on);
-                const uint8_t *dc8 = reinterpret_cast<const uint8_t *>(p.dc);
+                const uint8_t *on8 = reinterpret_cast<const uint8_t *>(p_on);
+                const uint8_t *dc8 = reinterpret_cast<const uint8_t *>(p_dc);
                 // 2^C <= 16 minterms: one byte, two for C = 4
                 x = on8[0];
                 if constexpr (C == 4) x |= (uint32_t)on8[1] << 8;
@@ -304,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
 
     // Count: one atomic per warp.
     for (int o = 16; o > 0; o >>= 1) bits += __shfl_down_sync(0xffffffffu, bits, o);
-    if ((threadIdx.x & 31) == 0 && bits) atomicAdd(p.count, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicAdd(p_count, bits);
     __syncthreads();
 
     // Dense bitmap: the tile is rows base .. base + R - 1 (B = 0, a = 0), i.e.
@@ -324,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
         const uint32_t val = extract32<C>(st, 32 * i - o, R);
         const bool shared_prev = (i == 0 && o != 0);
         const bool shared_next = (i == nw - 1 && !last_tile && tail != 0);
-        uint32_t *dst = p.out + W0 + i;
+        uint32_t *dst = p_out + W0 + i;
         if (!shared_prev && !shared_next) {
             *dst = val;
         } else {
@@ -337,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
     }
     if (last_tile)
         for (uint64_t w = p.out_words + threadIdx.x; w < p.out_alloc_words; w += blockDim.x)
-            p.out[w] = 0u;
+            p_out[w] = 0u;
 }
 
 // ------------------------------------------------------------------ dispatch
@@ -397,12 +416,13 @@ static cudaError_t dispatch_k(int C, const Pass &ps, const PassArgs &a, cudaStre
 
 cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
                          uint32_t *d_bitmap, unsigned long long *d_count, cudaStream_t stream, int first,
-                         int last)
+                         int last, const BatchArgs *batch)
 {
     if (last < 0) last = (int)plan.passes.size();
     if (first < 0 || last > (int)plan.passes.size() || first > last) return cudaErrorInvalidValue;
+    if (batch && batch->nfun == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if (first == 0) {
+    if (first == 0 && !batch) {
         e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
     }
@@ -415,8 +435,18 @@ cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc, v
     a.total_rows = pow3(plan.H);
     a.out_words = bitmap_words(plan.n);
     a.out_alloc_words = bitmap_alloc_bytes(plan.n) / 4;
+    if (batch) {
+        a.bfn = batch->fn;
+        a.btt_off = batch->tt_off;
+        a.bdc_off = batch->dc_off;
+        a.bbm_off = batch->bm_off;
+        a.barena = batch->arena;
+        a.bbitmaps = batch->bitmaps;
+        a.bcount = batch->count;
+    }
     for (int pi = first; pi < last; ++pi) {
-        const Pass &ps = plan.passes[pi];
+        Pass ps = plan.passes[pi];
+        if (batch) ps.tiles = batch->nfun;   // one-tile plans: a CTA per function
         a.n_mid = ps.n_mid;
         a.w_g = ps.w_g;
         a.w_top = ps.w_top;

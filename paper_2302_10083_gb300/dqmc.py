@@ -1,4 +1,5 @@
-"""ctypes binding of libdqmc.so (C ABI in include/dqmc.h and include/dqmc_plan.h).
+"""ctypes binding of libdqmc.so (C ABI in include/dqmc.h, include/dqmc_plan.h and
+include/dqmc_batch.h).
 
 Argument marshalling only: every step of the sweep runs in the library's CUDA
 kernels.  The functions named ``dqmc_*`` mirror the C entry points one to one;
@@ -63,6 +64,9 @@ _SIGS = {
                                            ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
     "dqmc_primes_dev_static": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "dqmc_batch_run": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p, c_vp]),
+    "dqmc_batch_workspace_bytes": (ctypes.c_uint64, [ctypes.c_uint32, c_u32p]),
+    "dqmc_batch_release": (ctypes.c_int, []),
 }
 
 
@@ -260,3 +264,51 @@ class DeviceBuffers:
         return dqmc_list_dev(self.n, self.on.data_ptr(), self.dc.data_ptr() if self.dc is not None else None,
                              self.bitmap.data_ptr(), self.pairs.data_ptr() if self.cap else None, self.cap,
                              self.count.data_ptr(), self.work.data_ptr(), self.work_bytes, s.cuda_stream)
+
+
+# ------------------------------------------------------------------ batch
+
+DQMC_BATCH_MAX_N = 14
+
+
+def _host_u32(a):
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return a, a.ctypes.data_as(c_u32p)
+
+
+def _host_u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(c_u64p)
+
+
+def batch_bitmap_layout(ns):
+    """Bitmap slots for a batch: byte offset of each function's bitmap
+    (dqmc_bitmap_alloc_bytes(n) bytes each, 16-aligned) and the total bytes."""
+    sizes = np.array([dqmc_bitmap_alloc_bytes(int(n)) for n in ns], dtype=np.uint64)
+    off = np.zeros(len(sizes), dtype=np.uint64)
+    if len(sizes):
+        off[1:] = np.cumsum(sizes)[:-1]
+    return off, int(sizes.sum())
+
+
+def dqmc_batch_workspace_bytes(ns) -> int:
+    a, p = _host_u32(ns)
+    return int(lib().dqmc_batch_workspace_bytes(len(a), p))
+
+
+def dqmc_batch_run(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, stream) -> int:
+    """dqmc_batch_run: ns / tt_off / dc_off / bm_off are host arrays (dc_off may
+    be None), the d_* arguments device pointers (ints), stream a cudaStream_t
+    (int or None).  Returns the status."""
+    n_a, n_p = _host_u32(ns)
+    tt_a, tt_p = _host_u64(tt_off)
+    bm_a, bm_p = _host_u64(bm_off)
+    if dc_off is None:
+        dc_a, dc_p = None, None
+    else:
+        dc_a, dc_p = _host_u64(dc_off)
+    return lib().dqmc_batch_run(len(n_a), n_p, tt_p, d_arena, dc_p, d_counts, d_bitmaps, bm_p, stream)
+
+
+def dqmc_batch_release() -> int:
+    return lib().dqmc_batch_release()

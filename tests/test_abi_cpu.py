@@ -70,6 +70,38 @@ def test_bad_arguments_rejected_without_gpu():
     assert L.dqmc_plan_json(26, None, 0) == dqmc.DQMC_EINVAL
 
 
+def test_batch_arguments_rejected_without_gpu():
+    L = dqmc.lib()
+    n = np.array([4, 14], dtype=np.uint32)
+    off = np.array([0, 16], dtype=np.uint64)
+    n_p = n.ctypes.data_as(dqmc.c_u32p)
+    o_p = off.ctypes.data_as(dqmc.c_u64p)
+    assert L.dqmc_batch_run(0, None, None, None, None, None, None, None, None) == dqmc.DQMC_OK
+    assert L.dqmc_batch_run(2, None, o_p, 256, None, 256, 256, o_p, None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_batch_run(2, n_p, o_p, None, None, 256, 256, o_p, None) == dqmc.DQMC_EINVAL
+    too_big = np.array([4, 15], dtype=np.uint32)
+    assert L.dqmc_batch_run(2, too_big.ctypes.data_as(dqmc.c_u32p), o_p, 256, None, 256, 256, o_p,
+                            None) == dqmc.DQMC_EINVAL
+    odd = np.array([0, 2], dtype=np.uint64)      # n = 14 table not 4-aligned; bitmap not 16-aligned
+    assert L.dqmc_batch_run(2, n_p, odd.ctypes.data_as(dqmc.c_u64p), 256, None, 256, 256, o_p,
+                            None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_batch_run(2, n_p, o_p, 256, None, 256, 256, odd.ctypes.data_as(dqmc.c_u64p),
+                            None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_batch_run(2, n_p, o_p, 256, None, 260, 256, o_p, None) == dqmc.DQMC_EINVAL  # counts
+
+
+def test_batch_workspace_and_layout():
+    # n <= 12 functions need no state; n = 13, 14 one padded state each
+    assert dqmc.dqmc_batch_workspace_bytes(np.array([4, 12])) < 1 << 16
+    w = dqmc.dqmc_batch_workspace_bytes(np.array([13, 14, 14]))
+    assert w >= (3 ** 8 + 2 * 3 ** 9) * 32
+    assert dqmc.dqmc_batch_workspace_bytes(np.array([15])) == 0
+    off, total = dqmc.batch_bitmap_layout([0, 4, 5, 14])
+    sizes = [dqmc.dqmc_bitmap_alloc_bytes(n) for n in (0, 4, 5, 14)]
+    assert list(off) == [0, sizes[0], sizes[0] + sizes[1], sum(sizes[:3])] and total == sum(sizes)
+    assert all(o % 16 == 0 for o in off)
+
+
 # ------------------------------------------------------------------ plan
 
 def plan(n):
