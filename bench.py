@@ -16,6 +16,13 @@ its own function (replicas, weak scaling; the passes need no exchange).
 cube, OpenMP on the host cores) on a bounded sample of the same workload
 family: the same generator and density at n = 19 per step.
 
+--workload serving (not the default line): Poisson arrivals at 1e2, 1e3, 1e4
+and 1e5 jobs/s of functions with n log-uniform in 6..22 and ON density
+uniform in [0.2, 0.95], replayed against the library's serving loop
+(continuous batching, admission by device-memory footprint) and against the
+same loop run one job at a time; p50/p99 latency (arrival to result) and
+jobs/s for both, and the two must give the same prime counts.
+
 --workload batched (not the default line): 65,536 independent functions, n
 uniform in 4..14, ON density uniform in [0.3, 0.9], 10% with a Bernoulli(0.05)
 don't-care set.  It times the batch as one CUDA-graph launch (dqmc_batch_run)
@@ -54,7 +61,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
+    ap.add_argument("--serve-jobs", type=int, default=2000, help="serving: jobs per arrival rate at most")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving: arrival span per rate at most")
     ap.add_argument("--batch", type=int, default=65536, help="functions in the batched workload")
     return ap.parse_args()
 
@@ -477,6 +486,62 @@ def run_batched(args, rank, world, local):
     return 0
 
 
+def run_serving(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2302_10083_gb300 import dqmc, synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dqmc.lib()
+    rates = [1e2, 1e3, 1e4, 1e5]
+    m_max = args.serve_jobs
+    req = synth.serving_requests(m_max, 1 + rank, rate=1.0)   # n, density, seed per job (times rescaled below)
+    ns = req["n"].astype(np.uint32)
+    tts = [synth.random_function(int(ns[j]), int(req["seed"][j]) & 0x7FFFFFFF, float(req["density"][j]))[0]
+           for j in range(m_max)]
+    budget = 64 << 30
+    per_rate = []
+    for lam in rates:
+        m = max(1, min(m_max, int(lam * args.serve_seconds)))
+        t_arr = synth.serving_requests(m, 1 + rank, rate=lam)["t_arrive"]
+        t_arr = t_arr - t_arr[0]
+        res = {}
+        for mode, name in ((dqmc.DQMC_SERVER_CONCURRENT, "continuous"), (dqmc.DQMC_SERVER_SERIAL, "one_by_one")):
+            with dqmc.Server(budget, streams=8, mode=mode) as srv:
+                counts, lat, span = srv.replay(t_arr, ns[:m], tts[:m])
+                st = srv.stats()
+            res[name] = {"jobs_per_s": m / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "span_s": span,
+                         "batched_launches": st["batches"], "jobs_in_batches": st["batched_jobs"],
+                         "peak_running": st["peak_running"], "peak_device_bytes": st["peak_bytes"],
+                         "counts": counts}
+        same = bool(np.array_equal(res["continuous"].pop("counts"), res["one_by_one"].pop("counts")))
+        if not same:
+            raise SystemExit(f"rate {lam}: served counts differ from one-by-one")
+        per_rate.append({"rate_jobs_per_s": lam, "jobs": m, **res,
+                         "p99_speedup": res["one_by_one"]["p99_ms"] / res["continuous"]["p99_ms"],
+                         "throughput_speedup": res["continuous"]["jobs_per_s"] / res["one_by_one"]["jobs_per_s"],
+                         "counts_identical": same})
+    top = per_rate[-1]
+    result = {
+        "metric": "served jobs/s at 1e5 arrivals/s (Poisson, n log-uniform 6..22), p50/p99 latency per rate",
+        "value": top["continuous"]["jobs_per_s"], "unit": "jobs/s", "n_gpus": world, "steps": len(rates),
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 bitwise", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, n = floor(exp(U(ln 6, ln 23))) clipped to 6..22, "
+                               "ON density U[0.2, 0.95], seed 1+rank; truth tables from host memory, "
+                               "counts back to host, bitmaps device-resident until the job is done",
+                   "budget_bytes": budget, "streams": 8, "parallelism": f"replicas x{world}"},
+        "per_rate": per_rate,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -484,6 +549,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched":
         return run_batched(args, rank, world, local)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -1,5 +1,5 @@
-"""ctypes binding of libdqmc.so (C ABI in include/dqmc.h, include/dqmc_plan.h and
-include/dqmc_batch.h).
+"""ctypes binding of libdqmc.so (C ABI in include/dqmc.h, include/dqmc_plan.h,
+include/dqmc_batch.h and include/dqmc_server.h).
 
 Argument marshalling only: every step of the sweep runs in the library's CUDA
 kernels.  The functions named ``dqmc_*`` mirror the C entry points one to one;
@@ -67,6 +67,19 @@ _SIGS = {
     "dqmc_batch_run": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p, c_vp]),
     "dqmc_batch_workspace_bytes": (ctypes.c_uint64, [ctypes.c_uint32, c_u32p]),
     "dqmc_batch_release": (ctypes.c_int, []),
+    "dqmc_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(c_vp)]),
+    "dqmc_server_destroy": (ctypes.c_int, [c_vp]),
+    "dqmc_server_job_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int]),
+    "dqmc_server_submit": (ctypes.c_int, [c_vp, ctypes.c_uint32, c_u8p, c_u8p, ctypes.c_uint32, c_u64p]),
+    "dqmc_server_query": (ctypes.c_int, [c_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), c_u64p,
+                                         ctypes.POINTER(c_vp), c_u64p, c_u64p]),
+    "dqmc_server_copy_bitmap": (ctypes.c_int, [c_vp, ctypes.c_uint64, c_u8p, ctypes.c_uint64]),
+    "dqmc_server_wait": (ctypes.c_int, [c_vp, ctypes.c_uint64, ctypes.c_uint32]),
+    "dqmc_server_free_job": (ctypes.c_int, [c_vp, ctypes.c_uint64]),
+    "dqmc_server_stats": (ctypes.c_int, [c_vp, c_u64p]),
+    "dqmc_server_replay": (ctypes.c_int, [c_vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double), c_u32p, c_vp,
+                                          c_vp, c_u64p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -312,3 +325,95 @@ def dqmc_batch_run(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, str
 
 def dqmc_batch_release() -> int:
     return lib().dqmc_batch_release()
+
+
+# ------------------------------------------------------------------ serving
+
+DQMC_SERVER_CONCURRENT = 0
+DQMC_SERVER_SERIAL = 1
+DQMC_JOB_DISCARD_BITMAP = 1
+DQMC_JOB_QUEUED, DQMC_JOB_RUNNING, DQMC_JOB_DONE = 0, 1, 2
+
+
+def dqmc_server_job_bytes(n: int, with_dc: bool = False) -> int:
+    return int(lib().dqmc_server_job_bytes(n, 1 if with_dc else 0))
+
+
+class Server:
+    """The library's serving loop (dqmc_server_*): jobs admitted by device-memory
+    footprint, small jobs batched on arrival, results device-resident."""
+
+    def __init__(self, hbm_bytes: int, streams: int = 8, mode: int = DQMC_SERVER_CONCURRENT):
+        h = c_vp()
+        _check(lib().dqmc_server_create(hbm_bytes, streams, mode, ctypes.byref(h)), "dqmc_server_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            st = lib().dqmc_server_destroy(self.h)
+            self.h = None
+            _check(st, "dqmc_server_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, n: int, on_bits, dc_bits=None, flags: int = 0) -> int:
+        on = _host_tt(on_bits, n)
+        dc = None if dc_bits is None else _host_tt(dc_bits, n)
+        job = ctypes.c_uint64()
+        _check(lib().dqmc_server_submit(self.h, n, _p8(on), None if dc is None else _p8(dc), flags,
+                                        ctypes.byref(job)), "dqmc_server_submit")
+        return job.value
+
+    def wait(self, job: int, timeout_ms: int = 600000) -> None:
+        _check(lib().dqmc_server_wait(self.h, job, timeout_ms), "dqmc_server_wait")
+
+    def query(self, job: int):
+        state, cnt, ptr = ctypes.c_int(), ctypes.c_uint64(), c_vp()
+        ts, td = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().dqmc_server_query(self.h, job, ctypes.byref(state), ctypes.byref(cnt), ctypes.byref(ptr),
+                                       ctypes.byref(ts), ctypes.byref(td)), "dqmc_server_query")
+        return {"state": state.value, "count": cnt.value, "d_bitmap": ptr.value, "t_submit_ns": ts.value,
+                "t_done_ns": td.value}
+
+    def bitmap(self, job: int, n: int) -> np.ndarray:
+        out = np.zeros(dqmc_bitmap_bytes(n), dtype=np.uint8)
+        _check(lib().dqmc_server_copy_bitmap(self.h, job, _p8(out), out.size), "dqmc_server_copy_bitmap")
+        return out
+
+    def free(self, job: int) -> None:
+        _check(lib().dqmc_server_free_job(self.h, job), "dqmc_server_free_job")
+
+    def stats(self) -> dict:
+        out = (ctypes.c_uint64 * 8)()
+        _check(lib().dqmc_server_stats(self.h, ctypes.cast(out, c_u64p)), "dqmc_server_stats")
+        keys = ("submitted", "done", "batches", "batched_jobs", "bytes_in_use", "peak_bytes", "peak_running",
+                "budget")
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def replay(self, t_arrive, ns, on_list, dc_list=None):
+        """Submit job j at t_arrive[j] s (ascending) after the call starts, wait
+        for all; returns (counts, latencies_s, span_s)."""
+        m = len(ns)
+        t = np.ascontiguousarray(t_arrive, dtype=np.float64)
+        n_a = np.ascontiguousarray(ns, dtype=np.uint32)
+        keep = [_host_tt(on_list[j], int(n_a[j])) for j in range(m)]
+        on_ptrs = (c_vp * m)(*[k.ctypes.data for k in keep])
+        dc_ptrs = None
+        if dc_list is not None:
+            dkeep = [None if d is None else _host_tt(d, int(n_a[j])) for j, d in enumerate(dc_list)]
+            keep += [d for d in dkeep if d is not None]
+            dc_ptrs = (c_vp * m)(*[None if d is None else d.ctypes.data for d in dkeep])
+        counts = np.zeros(m, dtype=np.uint64)
+        lat = np.zeros(m, dtype=np.float64)
+        span = ctypes.c_double()
+        st = lib().dqmc_server_replay(self.h, m, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      n_a.ctypes.data_as(c_u32p), ctypes.cast(on_ptrs, c_vp),
+                                      None if dc_ptrs is None else ctypes.cast(dc_ptrs, c_vp),
+                                      counts.ctypes.data_as(c_u64p),
+                                      lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(span))
+        _check(st, "dqmc_server_replay")
+        return counts, lat, span.value

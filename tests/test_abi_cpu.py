@@ -102,6 +102,30 @@ def test_batch_workspace_and_layout():
     assert all(o % 16 == 0 for o in off)
 
 
+def test_server_arguments_rejected_without_gpu():
+    import ctypes
+    L = dqmc.lib()
+    h = dqmc.c_vp()
+    assert L.dqmc_server_create(1 << 10, 4, 0, ctypes.byref(h)) == dqmc.DQMC_EINVAL   # budget < 1 MB
+    assert L.dqmc_server_create(1 << 30, 0, 0, ctypes.byref(h)) == dqmc.DQMC_EINVAL   # no stream
+    assert L.dqmc_server_create(1 << 30, 33, 0, ctypes.byref(h)) == dqmc.DQMC_EINVAL
+    assert L.dqmc_server_create(1 << 30, 4, 7, ctypes.byref(h)) == dqmc.DQMC_EINVAL   # mode
+    assert L.dqmc_server_create(1 << 30, 4, 0, None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_server_destroy(None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_server_submit(None, 4, None, None, 0, None) == dqmc.DQMC_EINVAL
+
+
+def test_server_job_bytes():
+    # a job holds its truth table(s), its bitmap slot and (n >= 13) its workspace
+    for n in (0, 5, 12, 13, 18, 22):
+        b = dqmc.dqmc_server_job_bytes(n)
+        assert b >= dqmc.dqmc_bitmap_alloc_bytes(n) + ((1 << n) + 7) // 8
+        if n >= 13:
+            assert b >= dqmc.dqmc_workspace_bytes(n)
+        assert dqmc.dqmc_server_job_bytes(n, True) > b
+    assert dqmc.dqmc_server_job_bytes(26) == 0
+
+
 # ------------------------------------------------------------------ plan
 
 def plan(n):
