@@ -297,7 +297,7 @@ struct PassShared {
     uint32_t warp_tot[kThreads / 32];
     uint32_t rcnt[3 * (kThreads / 32)];   // primes per warp region (bitmap pass)
     uint32_t tile_mask, tile_val;         // literal / value bits of the digits fixed per tile
-    int list_ok, overflow;
+    int list_ok, overflow, next_region;
     uint16_t c5[243];                     // copy of the chunk-cell table
     uint16_t code[kUnits];                // copy of the unit-digit table
     __device__ const FixedDigits &fix() const { return *reinterpret_cast<const FixedDigits *>(fix_raw); }
@@ -632,7 +632,13 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
 #pragma unroll 1
                 for (int k = 0; k < 3; ++k) {
                     uint32_t xr[kChunkWords];
-                    if (valid) finish_row(k, xr);
+                    if (valid) {
+                        finish_row(k, xr);
+                        if constexpr (MODE == kModeOut) {
+#pragma unroll
+                            for (int w = 0; w < kChunkWords; ++w) my_count += __popc(xr[w]);
+                        }
+                    }
                     __syncthreads();
                     if (valid) {
                         tile[uslot(u, 2 * k)] = make_uint4(xr[0], xr[1], xr[2], xr[3]);
@@ -659,12 +665,44 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
 
         if constexpr (MODE == kModeOut) {
             // ------------------------------------------------ bitmap and list
-            // The tile now holds the reduced rows.  Region r = units 32r ..
-            // belongs to one warp: count, dense bits into the region's own
-            // slots, bitmap store, then the region's pairs in those slots.
+            // The tile now holds the reduced rows, and the rounds counted
+            // them: the tile's count is published first, so that warp 0's
+            // look-back overlaps the other warps' regions.  Region r = units
+            // 32r .. goes to one warp (taken in turn): count, dense bits into
+            // the region's own slots, bitmap store, then the region's pairs
+            // in those slots.
+            uint32_t xs = my_count;
+            for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+            if (lane == 0) S.warp_tot[wid] = xs;
+            if (tid == 0) S.next_region = 0;
             __syncthreads();
+            uint32_t tile_total = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) tile_total += S.warp_tot[w];
+            if (tid == 0 && tile_total) atomicAdd(F.count, (unsigned long long)tile_total);
+            if (P.pairs && wid == 0) {
+                const uint64_t T = S.tile;
+                bool ok = true;
+                unsigned long long ex = 0;
+                if (ck(P, T < P.out_tiles, T)) {
+                    if (lane == 0)
+                        atomicExch(&P.status[T], (T == 0 ? kFlagP : kFlagA) | (unsigned long long)tile_total);
+                    ex = lookback_p(P, T, ok);
+                    if (lane == 0 && ok && T > 0) atomicExch(&P.status[T], kFlagP | (ex + tile_total));
+                } else {
+                    ok = false;
+                }
+                if (lane == 0) {
+                    S.excl = ex;
+                    S.list_ok = ok;
+                }
+            }
             constexpr int kRegions = (kUnits + 31) / 32;
-            for (int r = wid; r < kRegions; r += kThreads / 32) {
+            for (;;) {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(&S.next_region, 1);
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (r >= kRegions) break;
                 const int U0 = 32 * r;
                 const int nun = min(32, kUnits - U0);
                 const int u = U0 + lane;
@@ -686,7 +724,6 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                 for (int k = 0; k < 3; ++k)
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) c3 += __popc(x[k][w]);
-                my_count += c3;
                 // this unit's first pair among the region's (warp scan)
                 uint32_t incl = c3;
 #pragma unroll
@@ -829,34 +866,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         } else if constexpr (MODE == kModeOut) {
             if (last_tile)
                 for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += kThreads) out[w] = 0u;
-            // tile count
-            uint32_t xs = my_count;
-            for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-            if (lane == 0) S.warp_tot[wid] = xs;
-            __syncthreads();
-            uint32_t tile_total = 0;
-#pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) tile_total += S.warp_tot[w];
-            if (tid == 0 && tile_total) atomicAdd(F.count, (unsigned long long)tile_total);
             if (P.pairs) {
-                const uint64_t T = S.tile;
-                if (wid == 0) {
-                    bool ok = true;
-                    unsigned long long ex = 0;
-                    if (ck(P, T < P.out_tiles, T)) {
-                        if (lane == 0)
-                            atomicExch(&P.status[T], (T == 0 ? kFlagP : kFlagA) | (unsigned long long)tile_total);
-                        ex = lookback_p(P, T, ok);
-                        if (lane == 0 && ok && T > 0) atomicExch(&P.status[T], kFlagP | (ex + tile_total));
-                    } else {
-                        ok = false;
-                    }
-                    if (lane == 0) {
-                        S.excl = ex;
-                        S.list_ok = ok;
-                    }
-                }
-                __syncthreads();
+                __syncthreads();   // every region's pairs are in place, the look-back is done
                 const uint64_t cap = P.cap;
                 if (S.list_ok && !S.overflow) {
                     // each region's pairs to the list, region r = units 32r ..
