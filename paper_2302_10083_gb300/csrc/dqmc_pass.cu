@@ -16,8 +16,9 @@
 //
 // Per tile:
 //   load   the first pass reads truth-table words (tt_pass_kernel); the others
-//          read the units whose group digits are 0/1 (Merge input) or all
-//          units into shared memory (cp.async);
+//          copy the units whose group digits are 0/1 (Merge input) or all
+//          units into shared memory: cp.async, or bulk copies (TMA) on an
+//          mbarrier in the bitmap pass, whose tile is contiguous;
 //   Merge  the group digits one after another (Merge of Section 4.1: the
 //          '*' row becomes the AND of its 0 row and 1 row; '*' rows of an
 //          unmerged digit are zero in the state, so assignment equals the
@@ -48,11 +49,14 @@ namespace dqmc {
 static __constant__ MaskTable kMasksP = make_mask_table();
 
 constexpr int kUnits = kTileRows / 3;  // 729 units of three rows per tile
-// Shared memory of a unit pass: the tile (6 uint4 per unit), then one unit of
-// zeros that stands for the '*' neighbour a '*' digit does not have, then
-// (bitmap pass) one byte per row.
-constexpr int kZeroSlot = 6 * kUnits;
-constexpr size_t kUnitSmem = (size_t)(6 * kUnits + 6) * 16;
+// Shared memory of a unit pass, in 16-byte slots: the tile (6 slots per unit,
+// plus, in the padded layout, one free slot after every four units; see
+// uslot), then one unit of zeros that stands for the '*' neighbour a '*'
+// digit does not have.
+template <bool PAD>
+constexpr int tile_slots() { return 6 * kUnits + (PAD ? (kUnits + 3) / 4 : 0); }
+template <bool PAD>
+constexpr size_t unit_smem() { return (size_t)(tile_slots<PAD>() + 6) * 16; }
 
 // Lookup tables over tile units and the 5 chunk digits.
 struct PassTables {
@@ -158,14 +162,12 @@ constexpr int kThreads = 256;
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
-// Bitmap staging (last pass): a warp's 32 units are 96 rows = 768 words of
-// the tile; their 32 * 729 bits, starting at bit o < 32, take 730 words.  The
-// last warp of a tile has 729 - 22 * 32 = 25 units (600 words).
+// Bitmap staging (last pass): a region of 32 units spans 6 * 32 + 8 slots
+// (800 words); their 32 * 729 bits, starting at bit o < 32, take at most 730
+// words.  The last region has 729 - 22 * 32 = 25 units (6 * 25 + 6 slots).
 static_assert(kUnits == 22 * 32 + 25, "tile units");
-static_assert((31 + 32 * 729 + 31) / 32 <= 24 * 32, "full staging fits its rows");
-static_assert(4 * ((31 + 25 * 729 + 127) / 128) <= 24 * 25, "tail staging fits its rows");
-static_assert((31 + 729 * 24 + 486) / 32 + 9 <= 24 * 25, "tail list reads fit its rows");
-static_assert((31 + 729 * 31 + 486) / 32 + 9 <= 24 * 32, "list reads fit a warp's rows");
+static_assert((31 + 32 * 729 + 31) / 32 <= 4 * (6 * 32 + 8), "full staging fits its region");
+static_assert((31 + 25 * 729 + 31) / 32 <= 4 * (6 * 25 + 6), "tail staging fits its region");
 
 enum PassMode : int { kModeMerge = 0, kModeMergeReduce = 1, kModeReduce = 2, kModeOut = 3 };
 
@@ -184,19 +186,65 @@ __device__ __forceinline__ bool ck(const PassParams &P, bool cond, uint64_t idx)
 }
 
 // Shared-memory slot (uint4) of 16-byte piece c (row c/2, half c%2) of unit u.
-// Swapping the halves of every other group of four units keeps the eight
-// lanes of a quarter-warp on eight different 16-byte bank groups when they
-// read the same piece of consecutive units.
-__device__ __forceinline__ int uslot(int u, int c) { return 6 * u + (c ^ ((u >> 2) & 1)); }
+// Both layouts keep the eight lanes of a quarter-warp on eight different
+// 16-byte bank groups when they read the same piece of consecutive units:
+//   padded (PAD): the unit's 96 bytes are contiguous, as in the state (so a
+//     bulk copy moves four units at once), with one free slot after every four
+//     units (6u + u/4 mod 8 = 0 6 4 2 1 7 5 3);
+//   swizzled: every other group of four units has its row halves swapped,
+//     which also keeps units three apart (the Merge of unit digit 0) apart.
+template <bool PAD>
+__device__ __forceinline__ int uslot(int u, int c)
+{
+    if constexpr (PAD) return 6 * u + (u >> 2) + c;
+    else return 6 * u + (c ^ ((u >> 2) & 1));
+}
 
-// The first pass's tile layout: row r, half h.
-__device__ __forceinline__ int slotp(int r, int h) { return 2 * r + (h ^ ((r >> 2) & 1)); }
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
 
 __device__ __forceinline__ void cp_async16p(void *smem_dst, const void *gmem_src)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
 }
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bulk copy (TMA, no tensor map) of bytes (a multiple of 16, both addresses
+// 16-byte aligned) from global to shared memory, completing on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// The first pass's tile layout: row r, half h.
+__device__ __forceinline__ int slotp(int r, int h) { return 2 * r + (h ^ ((r >> 2) & 1)); }
 
 __device__ __forceinline__ uint64_t globaltimer_p()
 {
@@ -293,11 +341,12 @@ __device__ unsigned long long lookback_p(const PassParams &P, uint64_t T, bool &
 struct PassShared {
     alignas(8) unsigned char fix_raw[sizeof(FixedDigits)];  // FixedDigits, copied from the parameters
     uint64_t base, ttb, tile;
+    uint64_t bar;                         // mbarrier of the tile's bulk loads
     unsigned long long excl;
     uint32_t warp_tot[kThreads / 32];
     uint32_t rcnt[3 * (kThreads / 32)];   // primes per warp region (bitmap pass)
     uint32_t tile_mask, tile_val;         // literal / value bits of the digits fixed per tile
-    int list_ok, overflow, next_region;
+    int list_ok, overflow, next_region, load_fail;
     uint16_t c5[243];                     // copy of the chunk-cell table
     uint16_t code[kUnits];                // copy of the unit-digit table
     __device__ const FixedDigits &fix() const { return *reinterpret_cast<const FixedDigits *>(fix_raw); }
@@ -468,6 +517,9 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
     constexpr int RU = (B == 0) ? 1 : (int)pow3(B - 1);
     constexpr int D0 = (B == 0) ? 0 : B - 1;    // lowest group unit digit
     constexpr int NB = 1 << K;
+    constexpr bool PAD = (B == 0);   // the bitmap pass: padded layout, bulk loads
+    constexpr int kZeroSlot = tile_slots<PAD>();
+    auto uslot = [](int u, int c) { return dqmc::uslot<PAD>(u, c); };
     extern __shared__ uint4 tile[];
     __shared__ PassShared S;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -509,7 +561,47 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
     };
 
     // ---------------------------------------------------------------- load
-    {
+    // The bitmap pass's tile is one contiguous block of the state: bulk
+    // copies (TMA) of four units (384 bytes) at a time, completing on one
+    // mbarrier whose wait is bounded.  Other tiles are 96-byte runs far apart:
+    // cp.async of 16-byte pieces, consecutive lanes on consecutive pieces.
+    if constexpr (B == 0) {
+        if (tid == 0) {
+            S.load_fail = 0;
+            mbar_init(&S.bar, 1);
+            mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
+        }
+        __syncthreads();
+        for (int q = 4 * tid; q < kUnits; q += 4 * kThreads) {
+            const int nu = min(4, kUnits - q);
+            const uint64_t row0 = unit_row(q);
+            const uint64_t last = row0 + 3u * (uint64_t)nu - 1u;
+            if (!ck(P, last < state_rows, last)) continue;   // the wait below then gives up
+            bulk_g2s(&tile[uslot(q, 0)], &state[2 * row0], 96u * (uint32_t)nu, &S.bar);
+        }
+        if (tid < 6) tile[kZeroSlot + tid] = make_uint4(0u, 0u, 0u, 0u);
+        const uint64_t t0 = globaltimer_p();
+        while (!mbar_try_wait(&S.bar, 0)) {
+            if (globaltimer_p() - t0 > P.wait_ns) {
+                if (atomicCAS(P.ctrl, 0u, kErrTimeout) == 0u)
+                    printf("dqmc: tile load did not complete (block %d)\n", (int)blockIdx.x);
+                S.load_fail = 1;
+                break;
+            }
+        }
+        __syncthreads();
+        if (S.load_fail) {
+            // give copies still in flight a bounded time to land, then leave
+            if (tid == 0) {
+                const uint64_t t1 = globaltimer_p();
+                while (!mbar_try_wait(&S.bar, 0) && globaltimer_p() - t1 < P.wait_ns) {
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        if (tid == 0) mbar_inval(&S.bar);   // every thread has seen the tile land
+    } else {
         constexpr int units_in = (LOAD == kLoadSparse) ? NB * RU : kUnits;
         for (int p = tid; p < units_in * 6; p += kThreads) {
             const int q = p / 6, c = p - 6 * q;
@@ -524,8 +616,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         }
         if (tid < 6) tile[kZeroSlot + tid] = make_uint4(0u, 0u, 0u, 0u);
         asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
     }
-    __syncthreads();
 
     // --------------------------------------------------------------- Merge
     if constexpr (MODE == kModeMerge || MODE == kModeMergeReduce) {
@@ -583,8 +675,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             const int u = rd * kThreads + tid;
             const bool valid = u < kUnits;
             // Slots of the '*' neighbour of u in each group digit d: digit
-            // 0 -> u + 2*3^d, 1 -> u + 3^d, '*' -> the zero unit.
-            // se: even pieces (first row halves), so: odd pieces.
+            // 0 -> u + 2*3^d, 1 -> u + 3^d, '*' -> the zero unit; se: even
+            // pieces (first row halves), so: odd pieces.
             int se[6 - D0], so[6 - D0];
             {
                 const uint32_t code = valid ? (uint32_t)S.code[u] : 0u;
@@ -593,9 +685,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                     constexpr int Dd = (int)pow3(d);
                     const uint32_t lit = (code >> d) & 1u, one = (code >> (8 + d)) & 1u;
                     const int nb = u + (int)(2u - one) * Dd;
-                    const int sw = (nb >> 2) & 1;
-                    se[d - D0] = lit ? 6 * nb + sw : kZeroSlot;
-                    so[d - D0] = lit ? 6 * nb + 1 - sw : kZeroSlot + 1;
+                    se[d - D0] = lit ? uslot(nb, 0) : kZeroSlot;
+                    so[d - D0] = lit ? uslot(nb, 1) : kZeroSlot + 1;
                 });
             }
             // row k of the unit: OR of its '*' neighbours, chunk digits,
@@ -735,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                 if (lane == 0) S.rcnt[r] = wtot;
                 __syncwarp();   // every lane holds its rows: the region's slots are free
                 {
-                    uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + 6 * U0);
+                    uint32_t *const stg = reinterpret_cast<uint32_t *>(tile + uslot(U0, 0));
                     // these units are tile bits 729*U0 ..: words S0 .. of the
                     // bitmap, starting at bit o of word S0.  Unit 'lane' starts
                     // at bit lb0 of stg; its rows follow each other.  A word
@@ -882,7 +973,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                     for (int r = wid; r < kRegions; r += kThreads / 32) {
                         const uint32_t nr = __shfl_sync(0xffffffffu, rc, r);
                         const uint32_t off = __shfl_sync(0xffffffffu, ri, r) - nr;
-                        const uint2 *src = reinterpret_cast<const uint2 *>(tile + 6 * 32 * r);
+                        const uint2 *src = reinterpret_cast<const uint2 *>(tile + uslot(32 * r, 0));
                         const unsigned long long k0 = S.excl + off;
                         for (uint32_t i = lane; i < nr; i += 32)
                             if (k0 + i < cap) P.pairs[k0 + i] = src[i];
@@ -949,7 +1040,7 @@ constexpr uint64_t kStageStrideBytes = 1ull << 20;
 template <int K, int B, int LOAD, int MODE, int CM>
 static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
-    size_t smem = kUnitSmem;
+    size_t smem = unit_smem<B == 0>();
     if constexpr (MODE == kModeMergeReduce || MODE == kModeReduce)
         if (p.w_g * kChunkBytes >= kStageStrideBytes)
             return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream);
