@@ -158,7 +158,9 @@ __device__ __forceinline__ FnBufs fn_bufs(const PassParams &P)
     return f;
 }
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;       // threads per CTA of the first pass and the Reduce passes (80 registers)
+constexpr int kOutThreads = 384;    // threads per CTA of the bitmap pass and the Merge-only passes
+constexpr int kMaxWarps = kOutThreads / 32;
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
@@ -343,8 +345,8 @@ struct PassShared {
     uint64_t base, ttb, tile;
     uint64_t bar;                         // mbarrier of the tile's bulk loads
     unsigned long long excl;
-    uint32_t warp_tot[kThreads / 32];
-    uint32_t rcnt[3 * (kThreads / 32)];   // primes per warp region (bitmap pass)
+    uint32_t warp_tot[kMaxWarps];
+    uint32_t rcnt[32];                    // primes per 32-unit region (bitmap pass)
     uint32_t tile_mask, tile_val;         // literal / value bits of the digits fixed per tile
     int list_ok, overflow, next_region, load_fail;
     uint16_t c5[243];                     // copy of the chunk-cell table
@@ -362,7 +364,7 @@ __device__ __forceinline__ void decode_tile(const PassParams &P, PassShared &S, 
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&P.fix);
         uint32_t *dst = reinterpret_cast<uint32_t *>(S.fix_raw);
-        for (int i = tid; i < (int)(sizeof(FixedDigits) / 4); i += kThreads) dst[i] = src[i];
+        for (int i = tid; i < (int)(sizeof(FixedDigits) / 4); i += (int)blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
     if (tid == 0) {
@@ -509,9 +511,14 @@ __device__ __noinline__ void emit_from_bitmap(const PassParams &P, PassShared &S
 // B == 0: the bitmap pass (a = 0): unit u holds tile rows 3u .. 3u+2, i.e.
 //         state rows base + 3u + k; tile digit 0 and unit digits 0 .. 5 are
 //         the group digits.
+template <int MODE>
+constexpr int unit_threads() { return (MODE == kModeOut || MODE == kModeMerge) ? kOutThreads : kThreads; }
+
 template <int K, int B, int LOAD, int MODE, int CM, bool STAGE>
-__global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_constant__ PassParams P)
+__global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(const __grid_constant__ PassParams P)
 {
+    constexpr int NT = unit_threads<MODE>();
+    constexpr int kRounds = (kUnits + NT - 1) / NT;   // rounds of units per tile
     static_assert(K + B == kTileDigits, "tiles are 3^7 rows");
     static_assert(B >= 1 || (MODE == kModeOut && LOAD == kLoadFull), "B = 0 only in the bitmap pass");
     constexpr int RU = (B == 0) ? 1 : (int)pow3(B - 1);
@@ -526,9 +533,9 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
 
     const FnBufs F = fn_bufs(P);
     decode_tile<MODE == kModeOut>(P, S, F.tile);
-    for (int i = tid; i < kUnits; i += kThreads) S.code[i] = g_tab.code[i];
+    for (int i = tid; i < kUnits; i += NT) S.code[i] = g_tab.code[i];
     if constexpr (MODE == kModeOut) {
-        for (int i = tid; i < 243; i += kThreads) S.c5[i] = g_tab.c5[i];
+        for (int i = tid; i < 243; i += NT) S.c5[i] = g_tab.c5[i];
         if (tid == 0) {
             S.overflow = 0;
             // literal / value bits of the high digits >= 7 (fixed in this tile)
@@ -572,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
         }
         __syncthreads();
-        for (int q = 4 * tid; q < kUnits; q += 4 * kThreads) {
+        for (int q = 4 * tid; q < kUnits; q += 4 * NT) {
             const int nu = min(4, kUnits - q);
             const uint64_t row0 = unit_row(q);
             const uint64_t last = row0 + 3u * (uint64_t)nu - 1u;
@@ -603,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         if (tid == 0) mbar_inval(&S.bar);   // every thread has seen the tile land
     } else {
         constexpr int units_in = (LOAD == kLoadSparse) ? NB * RU : kUnits;
-        for (int p = tid; p < units_in * 6; p += kThreads) {
+        for (int p = tid; p < units_in * 6; p += NT) {
             const int q = p / 6, c = p - 6 * q;
             int u = q;
             if constexpr (LOAD == kLoadSparse) {
@@ -629,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             constexpr int j = decltype(J)::value;
             constexpr int Dj = (int)pow3(j);
             constexpr int items = RU * Dj * (1 << (K - 1 - j));
-            static_assert(items <= kThreads, "one unit per thread");
+            static_assert(items <= NT, "one unit per thread");
             if (tid < items) {
                 const int eh = tid % RU, rest = tid / RU;
                 const int lo = rest % Dj, hb = rest / Dj;
@@ -649,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         // Write the units the Merge created (a '*' in a group digit); the
         // others came from the state unchanged.
         constexpr uint32_t gmask = (0x3fu >> D0) << D0;
-        for (int p = tid; p < kUnits * 6; p += kThreads) {
+        for (int p = tid; p < kUnits * 6; p += NT) {
             const int u = p / 6, c = p - 6 * u;
             if (!(~(uint32_t)S.code[u] & gmask)) continue;
             const uint64_t row0 = unit_row(u);
@@ -671,8 +678,8 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
         // done, that row of the round's units is free: the reduce passes put
         // the reduced row back in place, the bitmap pass stages dense bits there.
 #pragma unroll 1
-        for (int rd = 0; rd < 3; ++rd) {
-            const int u = rd * kThreads + tid;
+        for (int rd = 0; rd < kRounds; ++rd) {
+            const int u = rd * NT + tid;
             const bool valid = u < kUnits;
             // Slots of the '*' neighbour of u in each group digit d: digit
             // 0 -> u + 2*3^d, 1 -> u + 3^d, '*' -> the zero unit; se: even
@@ -769,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             __syncthreads();
             uint32_t tile_total = 0;
 #pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) tile_total += S.warp_tot[w];
+            for (int w = 0; w < NT / 32; ++w) tile_total += S.warp_tot[w];
             if (tid == 0 && tile_total) atomicAdd(F.count, (unsigned long long)tile_total);
             if (P.pairs && wid == 0) {
                 const uint64_t T = S.tile;
@@ -948,7 +955,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             // reduced tile -> state, consecutive lanes on consecutive 16-byte
             // pieces of a unit's three rows
             __syncthreads();
-            for (int p = tid; p < kUnits * 6; p += kThreads) {
+            for (int p = tid; p < kUnits * 6; p += NT) {
                 const int uu = p / 6, c = p - 6 * uu;
                 const uint64_t row0 = unit_row(uu);
                 if (!ck(P, row0 + 2 < state_rows, row0 + 2)) continue;
@@ -956,7 +963,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
             }
         } else if constexpr (MODE == kModeOut) {
             if (last_tile)
-                for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += kThreads) out[w] = 0u;
+                for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += NT) out[w] = 0u;
             if (P.pairs) {
                 __syncthreads();   // every region's pairs are in place, the look-back is done
                 const uint64_t cap = P.cap;
@@ -970,7 +977,7 @@ __global__ void __launch_bounds__(kThreads, 3) unit_pass_kernel(const __grid_con
                         const uint32_t y = __shfl_up_sync(0xffffffffu, ri, off);
                         if (lane >= off) ri += y;
                     }
-                    for (int r = wid; r < kRegions; r += kThreads / 32) {
+                    for (int r = wid; r < kRegions; r += NT / 32) {
                         const uint32_t nr = __shfl_sync(0xffffffffu, rc, r);
                         const uint32_t off = __shfl_sync(0xffffffffu, ri, r) - nr;
                         const uint2 *src = reinterpret_cast<const uint2 *>(tile + uslot(32 * r, 0));
@@ -1020,13 +1027,14 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 // ------------------------------------------------------------------ dispatch
 
 template <typename Kern>
-static cudaError_t launch_tiles(Kern kern, size_t smem, const PassParams &p, uint64_t tiles, cudaStream_t stream)
+static cudaError_t launch_tiles(Kern kern, size_t smem, const PassParams &p, uint64_t tiles, cudaStream_t stream,
+                               int threads = kThreads)
 {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (tiles == 0) return cudaSuccess;
     if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)tiles, kThreads, smem, stream>>>(p);
+    kern<<<(unsigned)tiles, threads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -1043,8 +1051,9 @@ static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t
     size_t smem = unit_smem<B == 0>();
     if constexpr (MODE == kModeMergeReduce || MODE == kModeReduce)
         if (p.w_g * kChunkBytes >= kStageStrideBytes)
-            return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream);
-    return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, false>, smem, p, tiles, stream);
+            return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream,
+                                unit_threads<MODE>());
+    return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, false>, smem, p, tiles, stream, unit_threads<MODE>());
 }
 
 template <int LOAD, int MODE, int CM>
