@@ -49,6 +49,13 @@ int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const void *d_dc
                         uint64_t *d_count, void *d_work, uint64_t work_bytes,
                         void *stream);
 
+/* Enqueue passes first .. last-1 (0 <= first < last <= dqmc_plan_passes(n);
+ * arguments as dqmc_list_dev), the same as calling dqmc_sweep_pass_dev for
+ * each in turn.  Returns DQMC_EINVAL for a bad range. */
+int dqmc_sweep_passes_dev(uint32_t n, int first, int last, const void *d_on, const void *d_dc, void *d_bitmap,
+                          uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work, uint64_t work_bytes,
+                          void *stream);
+
 /* Self-test of the bounded device waits (no GPU fault, nothing hangs): zeroes
  * the control block of d_work, then runs one device wait on a counter that no
  * kernel ever sets, with a limit of wait_ns nanoseconds (at most 10^9).  A

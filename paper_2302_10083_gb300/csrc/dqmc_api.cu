@@ -445,6 +445,27 @@ extern "C" int dqmc_sweep_pass_dev(uint32_t n, int pass, const void *d_on, const
     return dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
 }
 
+extern "C" int dqmc_sweep_passes_dev(uint32_t n, int first, int last, const void *d_on, const void *d_dc,
+                                     void *d_bitmap, uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work,
+                                     uint64_t work_bytes, void *stream)
+{
+    if (first < 0 || last <= first || n > DQMC_MAX_N || (cap && !d_pairs) || (d_pairs && !aligned(d_pairs, 8)))
+        return DQMC_EINVAL;
+    if (d_pairs && !d_count) return DQMC_EINVAL;
+    const Plan plan = make_plan((int)n);
+    if (last > plan_passes(plan)) return DQMC_EINVAL;
+    if (plan.sps.empty()) {
+        for (int i = first; i < last; ++i) {
+            const int st = dqmc_sweep_pass_dev(n, i, d_on, d_dc, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes,
+                                               stream);
+            if (st) return st;
+        }
+        return DQMC_OK;
+    }
+    return sweep_dev(n, first, last, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream,
+                     cap ? d_pairs : nullptr, cap);
+}
+
 extern "C" int dqmc_selftest_timeout(uint32_t n, void *d_work, uint64_t work_bytes, uint64_t wait_ns, void *stream)
 {
     if (n > DQMC_MAX_N || !d_work || !aligned(d_work, 256) || wait_ns > 1000000000ull) return DQMC_EINVAL;

@@ -62,6 +62,8 @@ _SIGS = {
     "dqmc_pass_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int, ctypes.c_int]),
     "dqmc_sweep_pass_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
                                            ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
+    "dqmc_sweep_passes_dev": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
+                                             ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
     "dqmc_primes_dev_static": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dqmc_batch_run": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p, c_vp]),
