@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--serve-jobs", type=int, default=2000, help="serving: jobs per arrival rate at most")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving: arrival span per rate at most")
     ap.add_argument("--batch", type=int, default=65536, help="functions in the batched workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched: keep the built-in launch table instead of tuning it on the batch first")
     return ap.parse_args()
 
 
@@ -396,6 +398,14 @@ def run_batched(args, rank, world, local):
         if st != 0:
             raise dqmc.DqmcError(st, "dqmc_batch_run")
 
+    # autotuner (untimed): each n's launch shape, timed on this batch
+    tune_s, tune_ms = None, None
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        tune_ms = dqmc.dqmc_batch_autotune(ns, b["tt_off"], arena.data_ptr(), b["dc_off"], counts.data_ptr(),
+                                           bitmaps.data_ptr(), bm_off, sh, reps=3)
+        tune_s = time.perf_counter() - t_tune
+    table = {str(n): dqmc.dqmc_batch_get_config(int(n)) for n in sorted(set(int(x) for x in ns))}
     for _ in range(max(args.warmup, 1)):
         graph_run()
     torch.cuda.synchronize()
@@ -477,6 +487,8 @@ def run_batched(args, rank, world, local):
                                     "ms_per_step": ms_single, "api": "dqmc_primes_dev, one call per function"},
         "speedup_vs_one_launch_per_function": ms_single / ms,
         "results_identical": same,
+        "launch_table": {"autotuned": not args.no_autotune, "seconds": tune_s,
+                         "best_ms_per_n": tune_ms, "config_per_n": table},
         "e2e": {"value": world * nf / e2e_s, "unit": "functions/s", "h2d_bytes_per_step": int(b["arena"].size),
                 "d2h_bytes_per_step": 8 * nf},
         "clocks": clocks,

@@ -6,13 +6,23 @@
  * function at a time and has no counterpart to batching; the arithmetic and
  * the results are unchanged by it.
  *
- * How: functions are grouped by n.  Functions with n <= 12 are swept by one
- * CTA each, with the whole state in shared memory; functions with n = 13 and
- * 14 by the streaming pass kernels, one launch per pass for all functions of
- * that n, each function with its own device state in a library-owned
- * workspace.  The library captures the whole sequence into a CUDA graph and
- * launches the graph; a later call with the same functions and buffers
- * launches the same graph again.
+ * How: functions are grouped by n, and each n is swept by one of two paths
+ * (its launch configuration, below):
+ *   DQMC_BATCH_PATH_SMEM   (5 <= n <= 14) a function's whole state stays in
+ *       shared memory from truth table to bitmap: fns_per_cta functions per
+ *       CTA, threads_per_fn threads each, the high digits merged and reduced
+ *       digits_per_step at a time; or one function per cluster of
+ *       ctas_per_fn = 3 (n = 13, 14) or 9 (n = 14) CTAs, the top one or two
+ *       high digits spread over the cluster (distributed shared memory);
+ *   DQMC_BATCH_PATH_TILES  n <= 12: one CTA per function (the kernel of the
+ *       single-function sweep); n = 13, 14: the streaming pass kernels, one
+ *       launch per pass for all functions of that n, each function with its
+ *       own device state in a library-owned workspace.
+ * The library captures the launches into a CUDA graph (one branch per n) and
+ * launches the graph; a later call with the same functions, buffers and
+ * configurations launches the same graph again.  dqmc_batch_autotune times
+ * every launchable configuration of each n on a given batch and keeps the
+ * fastest.
  */
 #ifndef DQMC_BATCH_H
 #define DQMC_BATCH_H
@@ -27,6 +37,26 @@ extern "C" {
 
 /* Largest n a batch function may have. */
 #define DQMC_BATCH_MAX_N 14
+
+/* Paths of one n (dqmc_batch_config.path). */
+#define DQMC_BATCH_PATH_SMEM 0
+#define DQMC_BATCH_PATH_TILES 1
+
+/* Launch configuration of the functions of one n.  For the TILES path the
+ * other fields are ignored (reported as 256, 1, 2, 1).  SMEM needs
+ * 5 <= n <= 14, threads_per_fn a multiple of 32 (>= 32),
+ * 1 <= fns_per_cta <= 15, digits_per_step 2 or 3,
+ * threads_per_fn * fns_per_cta <= 1024, ctas_per_fn 1, 3 (n = 13, 14) or
+ * 9 (n = 14) with fns_per_cta = 1 when it is above 1, and
+ * fns_per_cta * 3^(n-5-c) * 32 bytes of shared memory per CTA <= 227 KB,
+ * c = 0, 1, 2 for 1, 3, 9 CTAs per function. */
+typedef struct {
+    uint32_t path;
+    uint32_t threads_per_fn;   /* threads per function (per CTA of a cluster) */
+    uint32_t fns_per_cta;
+    uint32_t digits_per_step;
+    uint32_t ctas_per_fn;
+} dqmc_batch_config;
 
 /* Sweep nfun functions on the current CUDA device, enqueued on `stream`
  * (a cudaStream_t; NULL = legacy default stream).
@@ -50,7 +80,7 @@ extern "C" {
  *   d_out_bitmaps  the bitmap slots, 16-byte aligned.
  *
  * The library owns the workspace (device states of the n = 13, 14
- * functions, per-class control blocks, the function tables) and the graph;
+ * functions on the TILES path, per-class control blocks, the function tables) and the graph;
  * both stay allocated until dqmc_batch_release.  Calls must not overlap on
  * the device (they share that workspace): order them on one stream, or
  * synchronise between them.  The call returns once the graph is enqueued;
@@ -68,6 +98,29 @@ int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, con
  * control blocks, states of the n = 13, 14 functions).  0 if an n is out of
  * range. */
 uint64_t dqmc_batch_workspace_bytes(uint32_t nfun, const uint32_t *n);
+
+/* The configuration used for functions of n variables (process-wide; the
+ * built-in defaults until set or tuned).  DQMC_EINVAL for n above
+ * DQMC_BATCH_MAX_N or a null pointer. */
+int dqmc_batch_get_config(uint32_t n, dqmc_batch_config *out);
+
+/* Set it.  DQMC_EINVAL if the configuration breaks a rule above.  The next
+ * dqmc_batch_run captures a new graph. */
+int dqmc_batch_set_config(uint32_t n, const dqmc_batch_config *cfg);
+
+/* Autotuner: for every n present in the batch (same arguments and rules as
+ * dqmc_batch_run), time each launchable configuration (the TILES path and
+ * every SMEM shape with threads_per_fn in 32..1024, fns_per_cta in
+ * {1,2,3,4,6,8}, digits_per_step 2 and 3, ctas_per_fn 1, 3, 9): one untimed run, then the mean of
+ * `reps` runs, each a launch of that n's functions alone on `stream`, timed
+ * with CUDA events.  The fastest becomes that n's configuration.  Blocks
+ * until done.  out_ms (NULL, or DQMC_BATCH_MAX_N + 1 floats) gets each n's
+ * best time in ms, -1 for n not in the batch.  The output buffers are
+ * overwritten by the trial runs; call dqmc_batch_run for the results.
+ * DQMC_EINVAL as for dqmc_batch_run, or reps outside 1..1000. */
+int dqmc_batch_autotune(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
+                        const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps, const uint64_t *bm_off,
+                        uint32_t reps, void *stream, float *out_ms);
 
 /* Free the current device's batch workspace and graph (after the work that
  * uses them is done).  Returns DQMC_OK or DQMC_ECUDA. */

@@ -7,11 +7,12 @@
  *
  * The server owns one block of device memory (its HBM budget) and a
  * scheduler thread.  Jobs wait in a queue until their footprint fits in the
- * budget: the device copy of their truth tables, their state (n >= 13) and
+ * budget: the device copy of their truth tables, their state (n >= 15) and
  * their bitmap.  Admitted jobs run while others are still running:
- *   * jobs with n <= 12 that are waiting together are swept by one batched
- *     launch (one CTA per function, the state in shared memory);
- *   * jobs with n >= 13 run on their own CUDA stream (several at a time).
+ *   * jobs with n <= 14 that are waiting together are swept by one batched
+ *     launch per n (whole functions in shared memory, the launch shapes of
+ *     dqmc_batch_get_config; a cluster of three CTAs per function at n = 14);
+ *   * jobs with n >= 15 run on their own CUDA stream (several at a time).
  * When a job's kernels are done, its state and tables are freed at once and
  * the next jobs are admitted; its bitmap stays in device memory until the
  * client frees the job (or at once, for DQMC_JOB_DISCARD_BITMAP).
@@ -45,7 +46,7 @@ typedef struct dqmc_server dqmc_server;
 
 /* Create a server on the current CUDA device.  hbm_bytes of device memory
  * are allocated now and shared by all jobs; streams (1..32) CUDA streams run
- * the n >= 13 jobs; mode is DQMC_SERVER_CONCURRENT or DQMC_SERVER_SERIAL.
+ * the n >= 15 jobs; mode is DQMC_SERVER_CONCURRENT or DQMC_SERVER_SERIAL.
  * Returns DQMC_OK (and *out), DQMC_EINVAL, DQMC_ENOMEM or DQMC_ECUDA. */
 int dqmc_server_create(uint64_t hbm_bytes, uint32_t streams, int mode, dqmc_server **out);
 

@@ -1,11 +1,18 @@
 // dqmc_batch.cu -- the batch driver: many independent functions, grouped by
-// n, swept by one launch per (n, pass) and captured into one CUDA graph.
+// n, one launch per n (per pass on the streaming path), captured into one
+// CUDA graph with one branch per n, and the autotuner that picks each n's
+// launch.
 //
 // Every function is swept as dqmc_primes sweeps one function (DenseQMC,
-// arXiv 2302.10083, Algorithm 3, Section 4.1).  n <= 12: the one-tile kernel,
-// one CTA per function, the whole state in shared memory.  n = 13, 14: the
-// streaming pass kernels in batch mode, block b on tile b % tiles of function
-// list[b / tiles], each function with its own state in the workspace.
+// arXiv 2302.10083, Algorithm 3, Section 4.1).  Two paths per n:
+//   * shared memory (5 <= n <= 14, dqmc_fn.cu): a function's whole state in
+//     shared memory (a cluster of three CTAs for n = 14), fpc functions per
+//     CTA, tg threads each, D high digits per step;
+//   * tiles: n <= 12 the one-tile kernel of dqmc_sweep.cu, one CTA per
+//     function; n = 13, 14 the streaming pass kernels in batch mode, each
+//     function with its own state in the workspace.
+// The autotuner times every launchable choice on the caller's batch and
+// keeps the fastest per n.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -20,6 +27,52 @@ namespace dqmc {
 namespace {
 
 constexpr int kClasses = DQMC_BATCH_MAX_N + 1;
+
+// The launch of one n: path, then the shared-memory kernel's shape.
+struct ClassConfig {
+    uint32_t path = DQMC_BATCH_PATH_TILES;
+    FnConfig fn;
+};
+
+ClassConfig default_config(int n)
+{
+    ClassConfig c;
+    if (n < kFnMinN) return c;
+    c.path = DQMC_BATCH_PATH_SMEM;
+    static const int tg[kClasses] = {0, 0, 0, 0, 0, 32, 32, 32, 32, 32, 32, 64, 256, 512, 512};
+    static const int fpc[kClasses] = {0, 0, 0, 0, 0, 8, 8, 8, 8, 8, 8, 2, 1, 1, 1};
+    c.fn.tg = tg[n];
+    c.fn.fpc = fpc[n];
+    c.fn.digits = 3;
+    c.fn.ctas = n == 14 ? 3 : 1;
+    return c;
+}
+
+std::mutex g_cfg_mu;
+ClassConfig g_cfg[kClasses];
+bool g_cfg_init = false;
+uint64_t g_cfg_gen = 1;     // bumped by every change; a graph records the one it was captured with
+
+void config_snapshot(ClassConfig out[kClasses], uint64_t *gen)
+{
+    std::lock_guard<std::mutex> g(g_cfg_mu);
+    if (!g_cfg_init) {
+        for (int c = 0; c < kClasses; ++c) g_cfg[c] = default_config(c);
+        g_cfg_init = true;
+    }
+    for (int c = 0; c < kClasses; ++c) out[c] = g_cfg[c];
+    if (gen) *gen = g_cfg_gen;
+}
+
+bool config_ok(int n, const ClassConfig &c)
+{
+    if (n < 0 || n >= kClasses) return false;
+    if (c.path == DQMC_BATCH_PATH_TILES) return true;
+    return c.path == DQMC_BATCH_PATH_SMEM && fn_config_ok(n, c.fn);
+}
+
+// The streaming path keeps a device state per function (n >= 13 only).
+bool needs_state(int n, const ClassConfig &c) { return c.path == DQMC_BATCH_PATH_TILES && n >= 13; }
 
 uint64_t align_up_b(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -39,7 +92,7 @@ struct BatchLayout {
     uint64_t total = 0;
 };
 
-BatchLayout batch_layout(uint32_t nfun, const uint32_t count[kClasses])
+BatchLayout batch_layout(uint32_t nfun, const uint32_t count[kClasses], const ClassConfig cfg[kClasses])
 {
     BatchLayout L;
     uint64_t at = 0;
@@ -52,7 +105,7 @@ BatchLayout batch_layout(uint32_t nfun, const uint32_t count[kClasses])
     L.bm_off = at;
     at = align_up_b(at + 8ull * nfun, 256);
     for (int c = 0; c < kClasses; ++c) {
-        if (!count[c]) continue;
+        if (!count[c] || !needs_state(c, cfg[c])) continue;
         const Plan p = make_plan(c);
         if (p.sps.empty()) continue;
         L.ctrl_off[c] = at;
@@ -69,7 +122,11 @@ struct BatchCache {
     void *work = nullptr;
     uint64_t work_cap = 0;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t branch[kClasses] = {};
+    cudaEvent_t fork = nullptr, join[kClasses] = {};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;     // autotuner timing
     cudaGraphExec_t exec = nullptr;
+    uint64_t cfg_gen = 0;
     // what the graph was captured for
     std::vector<uint32_t> n;
     std::vector<uint64_t> tt, dc, bm;
@@ -93,6 +150,13 @@ BatchCache *batch_cache(int *st)
     if (!g_batch[dev]) {
         BatchCache *c = new BatchCache();
         e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < kClasses && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&c->branch[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->t0);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->t1);
         if (e != cudaSuccess) {
             *st = map_err(e);
             delete c;
@@ -104,9 +168,9 @@ BatchCache *batch_cache(int *st)
 }
 
 bool same_batch(const BatchCache &c, uint32_t nfun, const uint32_t *n, const uint64_t *tt, const uint64_t *dc,
-                const uint64_t *bm, const void *arena, void *counts, void *bitmaps)
+                const uint64_t *bm, const void *arena, void *counts, void *bitmaps, uint64_t gen)
 {
-    if (!c.exec || c.n.size() != nfun || c.arena != arena || c.counts != counts || c.bitmaps != bitmaps) return false;
+    if (!c.exec || c.cfg_gen != gen || c.n.size() != nfun || c.arena != arena || c.counts != counts || c.bitmaps != bitmaps) return false;
     if (c.has_dc != (dc != nullptr)) return false;
     if (memcmp(c.n.data(), n, 4ull * nfun) || memcmp(c.tt.data(), tt, 8ull * nfun) ||
         memcmp(c.bm.data(), bm, 8ull * nfun))
@@ -114,7 +178,98 @@ bool same_batch(const BatchCache &c, uint32_t nfun, const uint32_t *n, const uin
     return !dc || !memcmp(c.dc.data(), dc, 8ull * nfun);
 }
 
+// Check a batch's arrays; count[] gets the functions per n.
+int check_batch(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
+                const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps, const uint64_t *bm_off,
+                uint32_t count[kClasses])
+{
+    if (nfun > (1u << 24) || !n || !tt_off || !bm_off || !d_tt_arena || !d_out_count || !d_out_bitmaps)
+        return DQMC_EINVAL;
+    if ((uintptr_t)d_tt_arena % 4 || (uintptr_t)d_out_count % 8 || (uintptr_t)d_out_bitmaps % 16)
+        return DQMC_EINVAL;
+    for (int c = 0; c < kClasses; ++c) count[c] = 0;
+    for (uint32_t f = 0; f < nfun; ++f) {
+        if (n[f] > DQMC_BATCH_MAX_N) return DQMC_EINVAL;
+        const uint64_t a = n[f] >= 5 ? 4 : 1;
+        if (tt_off[f] % a || bm_off[f] % 16) return DQMC_EINVAL;
+        if (dc_off && dc_off[f] != ~0ull && dc_off[f] % a) return DQMC_EINVAL;
+        ++count[n[f]];
+    }
+    return DQMC_OK;
+}
+
+// Make the workspace at least L.total bytes and copy the function tables in
+// (ids grouped by n, largest n first; class_at[n] = first index of n).
+int upload_tables(BatchCache &c, const BatchLayout &L, uint32_t nfun, const uint32_t *n, const uint64_t *tt_off,
+                  const uint64_t *dc_off, const uint64_t *bm_off, uint32_t class_at[kClasses], cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (c.work_cap < L.total) {
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+        c.exec = nullptr;
+        if (c.work) {
+            e = cudaStreamSynchronize(s);   // earlier launches may still use the old workspace
+            if (e == cudaSuccess) e = cudaFree(c.work);
+            c.work = nullptr;
+            c.work_cap = 0;
+            if (e != cudaSuccess) return map_err(e);
+        }
+        e = cudaMalloc(&c.work, L.total);
+        if (e != cudaSuccess) return map_err(e);
+        c.work_cap = L.total;
+    }
+    char *work = static_cast<char *>(c.work);
+    std::vector<uint32_t> ids;
+    ids.reserve(nfun);
+    for (int cl = kClasses - 1; cl >= 0; --cl) {
+        class_at[cl] = (uint32_t)ids.size();
+        for (uint32_t f = 0; f < nfun; ++f)
+            if ((int)n[f] == cl) ids.push_back(f);
+    }
+    std::vector<uint64_t> dcv(nfun, ~0ull);
+    if (dc_off) memcpy(dcv.data(), dc_off, 8ull * nfun);
+    // ordinary stream-ordered copies: the launches below run after them
+    e = cudaMemcpyAsync(work + L.fn_off, ids.data(), 4ull * nfun, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(work + L.tt_off, tt_off, 8ull * nfun, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(work + L.dc_off, dcv.data(), 8ull * nfun, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(work + L.bm_off, bm_off, 8ull * nfun, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors die at return
+    return map_err(e);
+}
+
+// Enqueue the sweep of every function of one n.
+cudaError_t launch_class(BatchCache &c, const BatchLayout &L, int cl, const ClassConfig &cc, uint32_t first,
+                         uint32_t count, const void *d_tt_arena, void *d_out_count, void *d_out_bitmaps,
+                         cudaStream_t s)
+{
+    char *work = static_cast<char *>(c.work);
+    BatchArgs b;
+    b.fn = reinterpret_cast<const uint32_t *>(work + L.fn_off) + first;
+    b.nfun = count;
+    b.tt_off = reinterpret_cast<const uint64_t *>(work + L.tt_off);
+    b.dc_off = reinterpret_cast<const uint64_t *>(work + L.dc_off);
+    b.bm_off = reinterpret_cast<const uint64_t *>(work + L.bm_off);
+    b.arena = static_cast<const uint8_t *>(d_tt_arena);
+    b.bitmaps = static_cast<uint8_t *>(d_out_bitmaps);
+    b.count = reinterpret_cast<unsigned long long *>(d_out_count);
+    if (cc.path == DQMC_BATCH_PATH_SMEM) return launch_fn_batch(cl, b, cc.fn, s);
+    const Plan p = make_plan(cl);
+    if (p.sps.empty()) return launch_sweep(p, nullptr, nullptr, nullptr, nullptr, nullptr, s, 0, -1, &b);
+    return launch_super(p, nullptr, nullptr, work + L.state_off[cl], nullptr, nullptr, nullptr, 0,
+                        work + L.ctrl_off[cl], s, 0, plan_passes(p), &b);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_in_smem(int n, const BatchArgs &b, cudaStream_t s)
+{
+    if (n < 0 || n > kFnMaxN) return cudaErrorInvalidValue;
+    if (n < kFnMinN) return launch_sweep(make_plan(n), nullptr, nullptr, nullptr, nullptr, nullptr, s, 0, -1, &b);
+    ClassConfig cfg[kClasses];
+    config_snapshot(cfg, nullptr);
+    const ClassConfig cc = cfg[n].path == DQMC_BATCH_PATH_SMEM ? cfg[n] : default_config(n);
+    return launch_fn_batch(n, b, cc.fn, s);
+}
 
 }  // namespace dqmc
 
@@ -128,7 +283,9 @@ extern "C" uint64_t dqmc_batch_workspace_bytes(uint32_t nfun, const uint32_t *n)
         if (n[f] > DQMC_BATCH_MAX_N) return 0;
         ++count[n[f]];
     }
-    return batch_layout(nfun, count).total;
+    ClassConfig cfg[kClasses];
+    config_snapshot(cfg, nullptr);
+    return batch_layout(nfun, count, cfg).total;
 }
 
 extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
@@ -136,88 +293,49 @@ extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *
                               const uint64_t *bm_off, void *stream)
 {
     if (nfun == 0) return DQMC_OK;
-    if (nfun > (1u << 24) || !n || !tt_off || !bm_off || !d_tt_arena || !d_out_count || !d_out_bitmaps)
-        return DQMC_EINVAL;
-    if ((uintptr_t)d_tt_arena % 4 || (uintptr_t)d_out_count % 8 || (uintptr_t)d_out_bitmaps % 16)
-        return DQMC_EINVAL;
-    uint32_t count[kClasses] = {};
-    for (uint32_t f = 0; f < nfun; ++f) {
-        if (n[f] > DQMC_BATCH_MAX_N) return DQMC_EINVAL;
-        const uint64_t a = n[f] >= 5 ? 4 : 1;
-        if (tt_off[f] % a || bm_off[f] % 16) return DQMC_EINVAL;
-        if (dc_off && dc_off[f] != ~0ull && dc_off[f] % a) return DQMC_EINVAL;
-        ++count[n[f]];
-    }
-    int st = DQMC_OK;
+    uint32_t count[kClasses];
+    int st = check_batch(nfun, n, tt_off, d_tt_arena, dc_off, d_out_count, d_out_bitmaps, bm_off, count);
+    if (st != DQMC_OK) return st;
     BatchCache *c = batch_cache(&st);
     if (!c) return st;
     std::lock_guard<std::mutex> g(c->mu);
+    ClassConfig cfg[kClasses];
+    uint64_t gen = 0;
+    config_snapshot(cfg, &gen);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (same_batch(*c, nfun, n, tt_off, dc_off, bm_off, d_tt_arena, d_out_count, d_out_bitmaps))
+    if (same_batch(*c, nfun, n, tt_off, dc_off, bm_off, d_tt_arena, d_out_count, d_out_bitmaps, gen))
         return map_err(cudaGraphLaunch(c->exec, s));
 
-    // ---- new batch: workspace, function tables, then capture the graph
-    const BatchLayout L = batch_layout(nfun, count);
-    cudaError_t e = cudaSuccess;
-    if (c->work_cap < L.total) {
-        if (c->exec) cudaGraphExecDestroy(c->exec);
-        c->exec = nullptr;
-        if (c->work) {
-            e = cudaStreamSynchronize(s);   // earlier launches may still use the old workspace
-            if (e == cudaSuccess) e = cudaFree(c->work);
-            c->work = nullptr;
-            c->work_cap = 0;
-            if (e != cudaSuccess) return map_err(e);
-        }
-        e = cudaMalloc(&c->work, L.total);
-        if (e != cudaSuccess) return map_err(e);
-        c->work_cap = L.total;
-    }
-    char *work = static_cast<char *>(c->work);
-    // function ids grouped by n, largest n first (the big classes start first)
-    std::vector<uint32_t> ids;
-    ids.reserve(nfun);
-    uint32_t class_at[kClasses] = {};
-    for (int cl = kClasses - 1; cl >= 0; --cl) {
-        class_at[cl] = (uint32_t)ids.size();
-        for (uint32_t f = 0; f < nfun; ++f)
-            if ((int)n[f] == cl) ids.push_back(f);
-    }
-    std::vector<uint64_t> dcv(nfun, ~0ull);
-    if (dc_off) memcpy(dcv.data(), dc_off, 8ull * nfun);
-    // the tables go in with ordinary copies (stream-ordered: the graph below
-    // runs after them)
-    e = cudaMemcpyAsync(work + L.fn_off, ids.data(), 4ull * nfun, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(work + L.tt_off, tt_off, 8ull * nfun, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(work + L.dc_off, dcv.data(), 8ull * nfun, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(work + L.bm_off, bm_off, 8ull * nfun, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors die at return
-    if (e != cudaSuccess) return map_err(e);
-
+    // ---- new batch: workspace, function tables, then capture the graph:
+    // zero the counts, then one branch per n (largest n first), joined at the end
+    const BatchLayout L = batch_layout(nfun, count, cfg);
+    uint32_t class_at[kClasses];
+    st = upload_tables(*c, L, nfun, n, tt_off, dc_off, bm_off, class_at, s);
+    if (st != DQMC_OK) return st;
     if (c->exec) cudaGraphExecDestroy(c->exec);
     c->exec = nullptr;
     cudaStream_t cs = c->cap_stream;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return map_err(e);
     cudaError_t le = cudaMemsetAsync(d_out_count, 0, 8ull * nfun, cs);
+    if (le == cudaSuccess) le = cudaEventRecord(c->fork, cs);
+    bool joined[kClasses] = {};
     for (int cl = kClasses - 1; cl >= 0 && le == cudaSuccess; --cl) {
         if (!count[cl]) continue;
-        BatchArgs b;
-        b.fn = reinterpret_cast<const uint32_t *>(work + L.fn_off) + class_at[cl];
-        b.nfun = count[cl];
-        b.tt_off = reinterpret_cast<const uint64_t *>(work + L.tt_off);
-        b.dc_off = reinterpret_cast<const uint64_t *>(work + L.dc_off);
-        b.bm_off = reinterpret_cast<const uint64_t *>(work + L.bm_off);
-        b.arena = static_cast<const uint8_t *>(d_tt_arena);
-        b.bitmaps = static_cast<uint8_t *>(d_out_bitmaps);
-        b.count = reinterpret_cast<unsigned long long *>(d_out_count);
-        const Plan p = make_plan(cl);
-        if (p.sps.empty())
-            le = launch_sweep(p, nullptr, nullptr, nullptr, nullptr, nullptr, cs, 0, -1, &b);
-        else
-            le = launch_super(p, nullptr, nullptr, work + L.state_off[cl], nullptr, nullptr, nullptr, 0,
-                              work + L.ctrl_off[cl], cs, 0, plan_passes(p), &b);
+        cudaStream_t bs = c->branch[cl];
+        le = cudaStreamWaitEvent(bs, c->fork, 0);
+        if (le == cudaSuccess)
+            le = launch_class(*c, L, cl, cfg[cl], class_at[cl], count[cl], d_tt_arena, d_out_count, d_out_bitmaps, bs);
+        if (le == cudaSuccess) le = cudaEventRecord(c->join[cl], bs);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, c->join[cl], 0);
+        joined[cl] = le == cudaSuccess;
     }
+    // every branch that was forked must be joined before the capture ends
+    for (int cl = 0; cl < kClasses && le != cudaSuccess; ++cl)
+        if (count[cl] && !joined[cl]) {
+            cudaEventRecord(c->join[cl], c->branch[cl]);
+            cudaStreamWaitEvent(cs, c->join[cl], 0);
+        }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -239,7 +357,132 @@ extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *
     c->arena = d_tt_arena;
     c->counts = d_out_count;
     c->bitmaps = d_out_bitmaps;
+    c->cfg_gen = gen;
     return map_err(cudaGraphLaunch(c->exec, s));
+}
+
+extern "C" int dqmc_batch_get_config(uint32_t n, dqmc_batch_config *out)
+{
+    if (n > DQMC_BATCH_MAX_N || !out) return DQMC_EINVAL;
+    ClassConfig cfg[kClasses];
+    config_snapshot(cfg, nullptr);
+    out->path = cfg[n].path;
+    out->threads_per_fn = (uint32_t)cfg[n].fn.tg;
+    out->fns_per_cta = (uint32_t)cfg[n].fn.fpc;
+    out->digits_per_step = (uint32_t)cfg[n].fn.digits;
+    out->ctas_per_fn = (uint32_t)cfg[n].fn.ctas;
+    return DQMC_OK;
+}
+
+static ClassConfig from_public(const dqmc_batch_config &c)
+{
+    ClassConfig cc;
+    cc.path = c.path;
+    cc.fn.tg = (int)c.threads_per_fn;
+    cc.fn.fpc = (int)c.fns_per_cta;
+    cc.fn.digits = (int)c.digits_per_step;
+    cc.fn.ctas = (int)c.ctas_per_fn;
+    if (cc.path == DQMC_BATCH_PATH_TILES) cc.fn = FnConfig{};
+    return cc;
+}
+
+extern "C" int dqmc_batch_set_config(uint32_t n, const dqmc_batch_config *cfg)
+{
+    if (n > DQMC_BATCH_MAX_N || !cfg) return DQMC_EINVAL;
+    if (cfg->threads_per_fn > 4096 || cfg->fns_per_cta > 64 || cfg->digits_per_step > 8 || cfg->ctas_per_fn > 64)
+        return DQMC_EINVAL;
+    const ClassConfig cc = from_public(*cfg);
+    if (!config_ok((int)n, cc)) return DQMC_EINVAL;
+    ClassConfig cur[kClasses];
+    config_snapshot(cur, nullptr);   // makes sure the defaults are in place
+    std::lock_guard<std::mutex> g(g_cfg_mu);
+    g_cfg[n] = cc;
+    ++g_cfg_gen;
+    return DQMC_OK;
+}
+
+extern "C" int dqmc_batch_autotune(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
+                                   const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps,
+                                   const uint64_t *bm_off, uint32_t reps, void *stream, float *out_ms)
+{
+    if (out_ms)
+        for (int c = 0; c < kClasses; ++c) out_ms[c] = -1.0f;
+    if (nfun == 0) return DQMC_OK;
+    if (reps == 0 || reps > 1000) return DQMC_EINVAL;
+    uint32_t count[kClasses];
+    int st = check_batch(nfun, n, tt_off, d_tt_arena, dc_off, d_out_count, d_out_bitmaps, bm_off, count);
+    if (st != DQMC_OK) return st;
+    BatchCache *c = batch_cache(&st);
+    if (!c) return st;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the workspace of the streaming path for every n, so that every choice can run
+    ClassConfig tiles[kClasses];
+    const BatchLayout L = batch_layout(nfun, count, tiles);
+    uint32_t class_at[kClasses];
+    st = upload_tables(*c, L, nfun, n, tt_off, dc_off, bm_off, class_at, s);
+    if (st != DQMC_OK) return st;
+    // the graph (if any) was captured for another workspace layout
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    c->exec = nullptr;
+
+    ClassConfig best[kClasses];
+    config_snapshot(best, nullptr);
+    for (int cl = 0; cl < kClasses; ++cl) {
+        if (!count[cl]) continue;
+        std::vector<ClassConfig> cand;
+        cand.push_back(ClassConfig{});     // the tile / streaming path
+        if (cl >= kFnMinN)
+            for (int ctas : {1, 3, 9})
+                for (int d : {2, 3})
+                    for (int tg : {32, 64, 128, 256, 512, 1024})
+                        for (int fpc : {1, 2, 3, 4, 6, 8}) {
+                            ClassConfig cc;
+                            cc.path = DQMC_BATCH_PATH_SMEM;
+                            cc.fn.tg = tg;
+                            cc.fn.fpc = fpc;
+                            cc.fn.digits = d;
+                            cc.fn.ctas = ctas;
+                            // no more functions per CTA than the class has
+                            if (fpc > 1 && (uint32_t)fpc > count[cl]) continue;
+                            if (fn_config_ok(cl, cc.fn)) cand.push_back(cc);
+                        }
+        float best_ms = -1.0f;
+        for (const ClassConfig &cc : cand) {
+            cudaError_t e = cudaSuccess;
+            for (uint32_t r = 0; r <= reps && e == cudaSuccess; ++r) {
+                if (r == 1) e = cudaEventRecord(c->t0, s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(d_out_count, 0, 8ull * nfun, s);
+                if (e == cudaSuccess)
+                    e = launch_class(*c, L, cl, cc, class_at[cl], count[cl], d_tt_arena, d_out_count, d_out_bitmaps, s);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(c->t1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(c->t1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->t0, c->t1);
+            if (e != cudaSuccess) {
+                // a choice that does not launch on this device (e.g. no room for a
+                // cluster) is skipped; an error that sticks to the context is not
+                cudaGetLastError();
+                const cudaError_t sticky = cudaStreamSynchronize(s);
+                if (sticky != cudaSuccess) return map_err(sticky);
+                continue;
+            }
+            ms /= (float)reps;
+            if (best_ms < 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best[cl] = cc;
+            }
+        }
+        if (out_ms) out_ms[cl] = best_ms;
+    }
+    {
+        std::lock_guard<std::mutex> gc(g_cfg_mu);
+        for (int cl = 0; cl < kClasses; ++cl)
+            if (count[cl]) g_cfg[cl] = best[cl];
+        ++g_cfg_gen;
+    }
+    return DQMC_OK;
 }
 
 extern "C" int dqmc_batch_release(void)

@@ -1,0 +1,536 @@
+// dqmc_fn.cu -- whole functions in shared memory, for batches of small and
+// medium functions (5 <= n <= 14).
+//
+// What is computed is the sweep of DenseQMC (arXiv 2302.10083, Algorithm 3 in
+// Section 4.1): MergeAll, S(u) |= S(s) & S(t) for every triple (s, t, u) that
+// differs only in one digit (values 0, 1, *), then ReduceAll,
+// S(s) &= ~S(u), S(t) &= ~S(u), and the dense bitmap and count of what is left
+// (the prime implicants; output as in Algorithm 4, Section 4.2).
+//
+// How it is scheduled:
+//   * One function's state (3^(n-5) rows of one 32-byte chunk, the layout of
+//     dqmc_chunk.cuh) stays in shared memory from the truth table to the
+//     bitmap: device memory sees the truth table once and the bitmap once.
+//   * A CTA holds fpc functions, each worked on by tg threads with a named
+//     barrier of its own.  Or a cluster of CL = 3 or 9 CTAs holds one function
+//     (n = 13, 14; n = 14 takes 598 KB): the top one or two high digits are
+//     the cluster digits, and CTA k holds the cubes whose cluster digits are
+//     the base-3 digits of k.  Merge of a cluster digit needs no exchange: the
+//     part with a '*' cluster digit is the Merge of the AND of the truth-table
+//     parts of its 0 and 1 values (a cube with a '*' there covers one minterm
+//     of each).  Reduce of a cluster digit reads the '*' CTA over distributed
+//     shared memory, one digit after the other.
+//   * The high digits are merged and reduced D at a time: a thread loads the
+//     3^D rows of one block (one 8-byte slice of each), does the D digits in
+//     registers and writes the block back.  Within one step the blocks are
+//     disjoint, so working in place reads the state the step started from.
+//     Merge goes from the lowest digit up, so a block only reads rows whose
+//     higher digits are 0/1 (the others are still empty); Reduce may take the
+//     digits in any order (the grouped form of ReduceAll, see dqmc_sweep.cu).
+//   * The chunk digits are reduced per row in registers with funnel shifts;
+//     each warp packs its 32 rows (243 words) in place, and the bitmap goes
+//     out in coalesced 16-byte stores.
+#include <cooperative_groups.h>
+
+#include "dqmc_chunk.cuh"
+#include "dqmc_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace dqmc {
+
+static __constant__ MaskTable kFnMasks = make_mask_table();
+
+struct FnArgs {
+    const uint32_t *fn;             // function ids of this launch (one n)
+    uint32_t nfun;
+    uint32_t tg;                    // threads per function (multiple of 32)
+    uint32_t fpc;                   // functions per CTA (1 for a cluster)
+    const uint64_t *tt_off, *dc_off, *bm_off;
+    const uint8_t *arena;
+    uint8_t *bitmaps;
+    unsigned long long *count;
+    uint64_t out_words, out_alloc_words;   // ceil(3^n / 32), bitmap slot in words
+};
+
+// Shared-memory layout of a function's rows: row r at bytes 32r .. 32r+31,
+// no swizzle.  A Merge / Reduce step has lanes 4k..4k+3 on the four 8-byte
+// slices of one row and eight rows per warp at an odd stride (3^j apart, or
+// consecutive), which spreads them over all four 128-byte bank phases: two
+// wavefronts per warp access, the least 256 bytes take.  Rows of a block are
+// then a fixed number of bytes apart, so one base address and compile-time
+// offsets reach all of them.
+__device__ __forceinline__ int fslot(int r, int h) { return 2 * r + h; }
+
+__device__ __forceinline__ void ld_row(const uint4 *S, int r, uint32_t (&v)[kChunkWords])
+{
+    const uint4 a = S[fslot(r, 0)], b = S[fslot(r, 1)];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__device__ __forceinline__ void st_row(uint4 *S, int r, const uint32_t (&v)[kChunkWords])
+{
+    S[fslot(r, 0)] = make_uint4(v[0], v[1], v[2], v[3]);
+    S[fslot(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
+// sum of 3^i over the set bits i of x (x < 2^K)
+template <int K>
+__device__ __forceinline__ int spread3k(int x)
+{
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r += ((x >> i) & 1) * (int)pow3(i);
+    return r;
+}
+
+// Compile-time digit helpers over block indices t < 3^D.
+__host__ __device__ constexpr int twos_of(int t, int D)
+{
+    int c = 0;
+    for (int i = 0; i < D; ++i, t /= 3) c += (t % 3) == 2;
+    return c;
+}
+__host__ __device__ constexpr bool binary_above(int t, int d, int D)
+{
+    for (int i = 0; i < D; ++i, t /= 3)
+        if (i > d && (t % 3) == 2) return false;
+    return true;
+}
+
+// The 32 minterms of a chunk -> its 243 cells, Merged over the five chunk
+// digits (before digit i is merged its '*' cells are zero, so OR equals
+// assignment).
+__device__ __forceinline__ void chunk_merge_from_tt(uint32_t x, uint32_t (&v)[kChunkWords])
+{
+#pragma unroll
+    for (int w = 0; w < kChunkWords; ++w) v[w] = 0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        const int q = spread_pos(t);
+        v[q >> 5] |= ((x >> t) & 1u) << (q & 31);
+    }
+    static_for<0, kChunkDigits>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int d = (int)pow3(i);
+        uint32_t nv[kChunkWords];
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w)
+            nv[w] = v[w] | (shl_word<d>(v, w) & shl_word<2 * d>(v, w) & kFnMasks.m[kChunkDigits][i][2][w]);
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w) v[w] = nv[w];
+    });
+}
+
+// Reduce of the five chunk digits of one row, all read from v.
+__device__ __forceinline__ void chunk_reduce_row(uint32_t (&v)[kChunkWords])
+{
+    uint32_t acc[kChunkWords];
+#pragma unroll
+    for (int w = 0; w < kChunkWords; ++w) acc[w] = 0;
+    static_for<0, kChunkDigits>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int d = (int)pow3(i);
+        uint32_t y[kChunkWords];
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w) y[w] = v[w] & kFnMasks.m[kChunkDigits][i][2][w];
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w) acc[w] |= shr_word<d>(y, w) | shr_word<2 * d>(y, w);
+    });
+#pragma unroll
+    for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
+}
+
+struct SubSync {
+    int id, nthreads;
+    bool whole;
+    __device__ __forceinline__ void operator()() const
+    {
+        if (whole) __syncthreads();
+        else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+    }
+};
+
+// Merge of digits J .. J+DD-1 (of the HL digits a CTA holds): blocks of
+// 3^DD rows whose lower digits take any value and whose higher digits are 0/1.
+template <int HL, int J, int DD>
+__device__ __forceinline__ void merge_step(uint4 *S, int lt, int tg)
+{
+    constexpr int P = (int)pow3(J);
+    constexpr int T = (int)pow3(DD);
+    constexpr int items = P * (1 << (HL - J - DD)) * 4;
+    for (int it = lt; it < items; it += tg) {
+        const int q = it & 3, r = it >> 2;
+        const int lo = r % P, hb = r / P;
+        const int base = lo + (int)pow3(J + DD) * spread3k<HL - J - DD>(hb);
+        uint2 *bp = reinterpret_cast<uint2 *>(S) + 4 * base + q;   // slice q of row base
+        uint2 x[T];
+        static_for<0, T>([&](auto Ti) {
+            constexpr int t = decltype(Ti)::value;
+            if constexpr (twos_of(t, DD) == 0) x[t] = bp[4 * t * P];
+        });
+        static_for<0, DD>([&](auto Di) {
+            constexpr int d = decltype(Di)::value;
+            constexpr int w = (int)pow3(d);
+            static_for<0, T>([&](auto Ti) {
+                constexpr int t = decltype(Ti)::value;
+                if constexpr ((t / w) % 3 == 2 && binary_above(t, d, DD)) {
+                    x[t].x = x[t - 2 * w].x & x[t - w].x;
+                    x[t].y = x[t - 2 * w].y & x[t - w].y;
+                }
+            });
+        });
+        static_for<0, T>([&](auto Ti) {
+            constexpr int t = decltype(Ti)::value;
+            if constexpr (twos_of(t, DD) > 0) bp[4 * t * P] = x[t];
+        });
+    }
+}
+
+// Reduce of digits J .. J+DD-1 over all rows: each cell loses its bit if one
+// of its '*' neighbours in these digits is set, all read from the block as
+// the step found it (rows are updated in order of their number of '*'
+// digits, so a row is overwritten only after every row that reads it).
+template <int HL, int J, int DD>
+__device__ __forceinline__ void reduce_step(uint4 *S, int lt, int tg)
+{
+    constexpr int P = (int)pow3(J);
+    constexpr int T = (int)pow3(DD);
+    constexpr int items = (int)pow3(HL - DD) * 4;
+    for (int it = lt; it < items; it += tg) {
+        const int q = it & 3, r = it >> 2;
+        const int lo = r % P, hi = r / P;
+        const int base = lo + hi * (int)pow3(J + DD);
+        uint2 *bp = reinterpret_cast<uint2 *>(S) + 4 * base + q;   // slice q of row base
+        uint2 x[T];
+        static_for<0, T>([&](auto Ti) {
+            constexpr int t = decltype(Ti)::value;
+            x[t] = bp[4 * t * P];
+        });
+        static_for<0, DD>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;   // number of '*' digits of the rows updated now
+            static_for<0, T>([&](auto Ti) {
+                constexpr int t = decltype(Ti)::value;
+                if constexpr (twos_of(t, DD) == k) {
+                    uint32_t ax = 0, ay = 0;
+                    static_for<0, DD>([&](auto Di) {
+                        constexpr int d = decltype(Di)::value;
+                        constexpr int w = (int)pow3(d);
+                        constexpr int td = (t / w) % 3;
+                        if constexpr (td != 2) {
+                            ax |= x[t + (2 - td) * w].x;
+                            ay |= x[t + (2 - td) * w].y;
+                        }
+                    });
+                    x[t].x &= ~ax;
+                    x[t].y &= ~ay;
+                }
+            });
+        });
+        static_for<0, T>([&](auto Ti) {
+            constexpr int t = decltype(Ti)::value;
+            if constexpr (twos_of(t, DD) < DD) bp[4 * t * P] = x[t];
+        });
+    }
+}
+
+template <int HL, int J, int D>
+__device__ __forceinline__ void merge_all(uint4 *S, int lt, int tg, const SubSync &sync)
+{
+    if constexpr (J < HL) {
+        constexpr int DD = (HL - J < D) ? HL - J : D;
+        merge_step<HL, J, DD>(S, lt, tg);
+        sync();
+        merge_all<HL, J + DD, D>(S, lt, tg, sync);
+    }
+}
+
+template <int HL, int J, int D>
+__device__ __forceinline__ void reduce_all(uint4 *S, int lt, int tg, const SubSync &sync)
+{
+    if constexpr (J < HL) {
+        constexpr int DD = (HL - J < D) ? HL - J : D;
+        reduce_step<HL, J, DD>(S, lt, tg);
+        sync();
+        reduce_all<HL, J + DD, D>(S, lt, tg, sync);
+    }
+}
+
+template <int H, int CL, int D>
+__global__ void __launch_bounds__(1024, 1) fn_kernel(const FnArgs a)
+{
+    static_assert(CL == 1 || CL == 3 || CL == 9, "clusters of 1, 3 or 9 CTAs");
+    constexpr int CD = (CL == 9) ? 2 : (CL == 3) ? 1 : 0;   // cluster digits
+    constexpr int HL = H - CD;                              // high digits one CTA holds
+    constexpr int R = (int)pow3(HL);
+    constexpr int NB = 1 << HL;
+    extern __shared__ uint4 fsmem[];
+
+    const int tg = (int)a.tg;
+    const int sub = (int)threadIdx.x / tg, lt = (int)threadIdx.x - sub * tg;
+    int rank = 0;
+    if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
+    const uint64_t fi = (uint64_t)(blockIdx.x / CL) * a.fpc + sub;
+    if (fi >= a.nfun) return;   // a whole sub-group (or a whole cluster) leaves together
+    const SubSync sync{sub + 1, tg, a.fpc == 1};
+    uint4 *S = fsmem + (size_t)sub * 2 * R;
+
+    const uint32_t id = a.fn[fi];
+    const uint32_t *on = reinterpret_cast<const uint32_t *>(a.arena + a.tt_off[id]);
+    const uint64_t dco = a.dc_off[id];
+    const uint32_t *dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(a.arena + dco);
+    uint32_t *out = reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]);
+
+    // Load: the binary rows from the truth table (word g holds the 32 minterms
+    // of binary row g), chunk digits merged on the way.
+    // Cluster digit c of this CTA is digit c of rank; word gb + 2^HL b0 +
+    // 2^(HL+1) b1 holds binary row gb with cluster digits (b0, b1); a '*'
+    // cluster digit ANDs both values.
+    const int cd0 = CD >= 1 ? rank % 3 : 0, cd1 = CD >= 2 ? rank / 3 : 0;
+    for (int gb = lt; gb < NB; gb += tg) {
+        uint32_t x = 0xffffffffu;
+#pragma unroll
+        for (int b1 = 0; b1 < (CD >= 2 ? 2 : 1); ++b1) {
+            if (CD >= 2 && cd1 != 2 && b1 != cd1) continue;
+#pragma unroll
+            for (int b0 = 0; b0 < (CD >= 1 ? 2 : 1); ++b0) {
+                if (CD >= 1 && cd0 != 2 && b0 != cd0) continue;
+                const int wi = gb + (b0 << HL) + (b1 << (HL + 1));
+                x &= __ldg(on + wi) | (dc ? __ldg(dc + wi) : 0u);
+            }
+        }
+        uint32_t v[kChunkWords];
+        chunk_merge_from_tt(x, v);
+        st_row(S, spread3k<HL>(gb), v);
+    }
+    sync();
+    merge_all<HL, 0, D>(S, lt, tg, sync);
+
+    if constexpr (CL > 1) {
+        // Reduce of the cluster digits, one after the other: for digit c, the
+        // CTAs whose digit c is 0 or 1 clear what the CTA with a '*' there
+        // (merged, and not modified in this step) has set.
+        cg::cluster_group cl = cg::this_cluster();
+        static_for<0, CD>([&](auto Ci) {
+            constexpr int c = decltype(Ci)::value;
+            constexpr int wc = (int)pow3(c);
+            cl.sync();
+            const int dgt = (rank / wc) % 3;
+            if (dgt != 2) {
+                const uint4 *T = cl.map_shared_rank(fsmem, rank + (2 - dgt) * wc);
+                // eight remote loads in flight per thread
+                constexpr int U = 8;
+                for (int i0 = lt; i0 < 2 * R; i0 += U * tg) {
+                    uint4 z[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int i = i0 + u * tg;
+                        z[u] = i < 2 * R ? T[i] : make_uint4(0u, 0u, 0u, 0u);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int i = i0 + u * tg;
+                        if (i < 2 * R) {
+                            uint4 v = S[i];
+                            v.x &= ~z[u].x; v.y &= ~z[u].y; v.z &= ~z[u].z; v.w &= ~z[u].w;
+                            S[i] = v;
+                        }
+                    }
+                }
+            }
+        });
+        cl.sync();   // no CTA changes its rows (or leaves) while another still reads them
+    }
+    reduce_all<HL, 0, D>(S, lt, tg, sync);
+
+    // Chunk digits, count, and the rows packed into the dense stream in
+    // place: a warp takes regions of 32 rows (1 KB of shared memory; 32 rows
+    // of 243 cells are exactly 243 words), reduces each row's chunk digits in
+    // registers and writes the region's packed words to its start.  Lane l's
+    // row starts at bit 243 l of the region; the word it shares with the next
+    // row is completed by the next lane.
+    constexpr int C3 = (int)pow3(kChunkDigits);
+    constexpr int NREG = (R + 31) / 32;
+    constexpr int NP = (int)(((uint64_t)R * C3 + 31) / 32);   // packed words of this CTA
+    const int lane = (int)threadIdx.x & 31, nwarp = tg >> 5;
+    uint32_t *Sw = reinterpret_cast<uint32_t *>(S);
+    unsigned long long bits = 0;
+    {
+        const int sh = (C3 * lane) & 31, w0 = (C3 * lane) >> 5;
+        const bool k8 = sh + C3 > 256;                     // the row's last word is word 8 (else 7)
+        const bool shares = ((sh + C3) & 31) != 0;         // the next row starts inside it
+        for (int g = lt >> 5; g < NREG; g += nwarp) {
+            const int r = 32 * g + lane;
+            uint32_t v[kChunkWords];
+            if (r < R) {
+                ld_row(S, r, v);
+                chunk_reduce_row(v);
+            } else {
+#pragma unroll
+                for (int w = 0; w < kChunkWords; ++w) v[w] = 0;
+            }
+#pragma unroll
+            for (int w = 0; w < kChunkWords; ++w) bits += __popc(v[w]);
+            uint32_t o[kChunkWords + 1];
+            o[0] = __funnelshift_l(0u, v[0], sh);
+#pragma unroll
+            for (int k = 1; k < kChunkWords; ++k) o[k] = __funnelshift_l(v[k - 1], v[k], sh);
+            o[kChunkWords] = __funnelshift_l(v[kChunkWords - 1], 0u, sh);
+            const uint32_t tailw = k8 ? o[8] : o[7];
+            const uint32_t from_prev = __shfl_up_sync(0xffffffffu, tailw, 1);
+            if (lane > 0 && sh != 0) o[0] |= from_prev;
+            __syncwarp();   // every row of the region is in registers before it is overwritten
+            if (r < R) {
+                const bool own_last = !shares || lane == 31 || r + 1 >= R;
+                uint32_t *dst = Sw + 256 * g + w0;
+#pragma unroll
+                for (int k = 0; k < 7; ++k) dst[k] = o[k];
+                if (k8 || own_last) dst[7] = o[7];
+                if (k8 && own_last) dst[8] = o[8];
+            }
+            __syncwarp();
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) bits += __shfl_down_sync(0xffffffffu, bits, off);
+    if (lane == 0 && bits) atomicAdd(a.count + id, bits);
+    sync();
+
+    // Packed word j of this CTA's stream is at word 256 (j / 243) + j % 243.
+    auto packed = [&](int j) -> uint32_t {
+        if (j < 0 || j >= NP) return 0u;
+        const int g = j / C3;
+        return Sw[256 * g + (j - g * C3)];
+    };
+    if constexpr (CL == 1) {
+        // The whole bitmap slot in 16-byte stores (zeros past the stream).
+        const int n4 = (int)(a.out_alloc_words / 4);
+        uint4 *out4 = reinterpret_cast<uint4 *>(out);
+        for (int q = lt; q < n4; q += tg) {
+            const int j = 4 * q;
+            out4[q] = make_uint4(packed(j), packed(j + 1), packed(j + 2), packed(j + 3));
+        }
+    } else {
+        // CTA `rank` holds rows rank*R .. rank*R + R-1 of the function: its
+        // stream starts at bit rank*R*243.  Words shared with the neighbouring
+        // CTA of the cluster are written with masked atomics.
+        const uint64_t bit0 = (uint64_t)rank * R * C3;
+        const int o = (int)(bit0 & 31);
+        const uint64_t W0 = bit0 >> 5;
+        constexpr uint64_t L = (uint64_t)R * C3;
+        const int nw = (int)((o + L + 31) >> 5);
+        const bool last = rank == CL - 1;
+        const int tail = (int)((o + L) & 31);
+        for (int i = lt; i < nw; i += tg) {
+            const uint32_t val = o ? __funnelshift_l(packed(i - 1), packed(i), o) : packed(i);
+            const bool shared_prev = (i == 0 && o != 0);
+            const bool shared_next = (i == nw - 1 && !last && tail != 0);
+            uint32_t *dst = out + W0 + i;
+            if (!shared_prev && !shared_next) {
+                *dst = val;
+            } else {
+                uint32_t m = 0xffffffffu;
+                if (shared_prev) m &= 0xffffffffu << o;
+                if (shared_next) m &= (1u << tail) - 1u;
+                atomicAnd(dst, val | ~m);
+                atomicOr(dst, val & m);
+            }
+        }
+        if (last)
+            for (uint64_t w = a.out_words + lt; w < a.out_alloc_words; w += tg) out[w] = 0u;
+    }
+}
+
+template <int H, int CL, int D>
+static cudaError_t launch_fn_t(const FnArgs &a, uint32_t ctas, size_t smem, cudaStream_t s)
+{
+    auto kern = fn_kernel<H, CL, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && CL > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas * CL);
+    cfg.blockDim = dim3(a.tg * a.fpc);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (CL > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int D>
+static cudaError_t launch_fn_d(int n, int cl, const FnArgs &a, uint32_t ctas, size_t smem, cudaStream_t s)
+{
+    if (cl == 3) {
+        if (n == 13) return launch_fn_t<8, 3, D>(a, ctas, smem, s);
+        if (n == 14) return launch_fn_t<9, 3, D>(a, ctas, smem, s);
+        return cudaErrorInvalidValue;
+    }
+    if (cl == 9) return n == 14 ? launch_fn_t<9, 9, D>(a, ctas, smem, s) : cudaErrorInvalidValue;
+    if (cl != 1) return cudaErrorInvalidValue;
+    switch (n) {
+    case 5: return launch_fn_t<0, 1, D>(a, ctas, smem, s);
+    case 6: return launch_fn_t<1, 1, D>(a, ctas, smem, s);
+    case 7: return launch_fn_t<2, 1, D>(a, ctas, smem, s);
+    case 8: return launch_fn_t<3, 1, D>(a, ctas, smem, s);
+    case 9: return launch_fn_t<4, 1, D>(a, ctas, smem, s);
+    case 10: return launch_fn_t<5, 1, D>(a, ctas, smem, s);
+    case 11: return launch_fn_t<6, 1, D>(a, ctas, smem, s);
+    case 12: return launch_fn_t<7, 1, D>(a, ctas, smem, s);
+    case 13: return launch_fn_t<8, 1, D>(a, ctas, smem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+uint64_t fn_smem_bytes(int n, int fpc, int ctas)
+{
+    if (n < kFnMinN || n > kFnMaxN) return 0;
+    const int cd = ctas == 9 ? 2 : ctas == 3 ? 1 : 0;
+    return (uint64_t)fpc * pow3(n - kChunkDigits - cd) * kChunkBytes;
+}
+
+bool fn_config_ok(int n, const FnConfig &c)
+{
+    if (n < kFnMinN || n > kFnMaxN) return false;
+    if (c.digits != 2 && c.digits != 3) return false;
+    if (c.tg < 32 || c.tg % 32 || c.fpc < 1 || c.fpc > 15) return false;
+    if (c.tg * c.fpc > 1024) return false;
+    // clusters: 3 CTAs for n = 13 and 14, 9 for n = 14, one function each
+    if (c.ctas == 3 && n != 13 && n != 14) return false;
+    if (c.ctas == 9 && n != 14) return false;
+    if (c.ctas != 1 && c.ctas != 3 && c.ctas != 9) return false;
+    if (c.ctas > 1 && c.fpc != 1) return false;
+    return fn_smem_bytes(n, c.fpc, c.ctas) <= kFnMaxSmem;
+}
+
+cudaError_t launch_fn_batch(int n, const BatchArgs &b, const FnConfig &c, cudaStream_t s)
+{
+    if (!fn_config_ok(n, c)) return cudaErrorInvalidValue;
+    if (b.nfun == 0) return cudaSuccess;
+    FnArgs a{};
+    a.fn = b.fn;
+    a.nfun = b.nfun;
+    a.tg = (uint32_t)c.tg;
+    a.fpc = (uint32_t)c.fpc;
+    a.tt_off = b.tt_off;
+    a.dc_off = b.dc_off;
+    a.bm_off = b.bm_off;
+    a.arena = b.arena;
+    a.bitmaps = b.bitmaps;
+    a.count = b.count;
+    a.out_words = bitmap_words(n);
+    a.out_alloc_words = bitmap_alloc_bytes(n) / 4;
+    const uint32_t groups = (b.nfun + c.fpc - 1) / c.fpc;   // CTAs, or clusters
+    const size_t smem = fn_smem_bytes(n, c.fpc, c.ctas);
+    return c.digits >= 3 ? launch_fn_d<3>(n, c.ctas, a, groups, smem, s)
+                         : launch_fn_d<2>(n, c.ctas, a, groups, smem, s);
+}
+
+}  // namespace dqmc

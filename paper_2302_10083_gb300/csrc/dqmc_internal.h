@@ -173,6 +173,29 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
 // Test hook: a device wait on a counter nothing sets; it must time out.
 cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wait_ns, cudaStream_t stream);
 
+// Whole functions in shared memory (dqmc_fn.cu), 5 <= n <= 14: tg threads
+// per function, fpc functions per CTA, the high digits merged and reduced
+// `digits` (2 or 3) at a time; or one function per cluster of ctas = 3
+// (n = 13, 14) or 9 (n = 14) CTAs.
+constexpr int kFnMinN = 5;
+constexpr int kFnMaxN = 14;
+constexpr uint64_t kFnMaxSmem = 232448;    // 227 KB of shared memory per CTA
+struct FnConfig {
+    int tg = 256;
+    int fpc = 1;
+    int digits = 2;
+    int ctas = 1;
+};
+uint64_t fn_smem_bytes(int n, int fpc, int ctas);
+bool fn_config_ok(int n, const FnConfig &c);
+// Counts are not zeroed; bitmaps and counts come from the batch tables.
+cudaError_t launch_fn_batch(int n, const BatchArgs &b, const FnConfig &c, cudaStream_t s);
+
+// Sweep a batch of functions of one n <= 14 without device state: the
+// shared-memory kernel with the batch table's shape for n (its default
+// shape if the table says the tile path), the one-tile kernel below n = 5.
+cudaError_t launch_batch_in_smem(int n, const BatchArgs &b, cudaStream_t s);
+
 // Enqueue compaction of a dense bitmap into (mask, value) pairs.
 constexpr int kListWordsPerBlock = 4096;
 cudaError_t launch_compact(int n, const uint32_t *d_bitmap, uint32_t *d_pairs, uint64_t cap,

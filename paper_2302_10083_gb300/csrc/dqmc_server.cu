@@ -3,9 +3,10 @@
 // completion signalled by host callbacks.
 //
 // Each job is swept as dqmc_primes sweeps one function (DenseQMC, arXiv
-// 2302.10083, Algorithm 3, Section 4.1), with the same kernels: the one-tile
-// kernel (n <= 12; in batch mode when several small jobs wait together) and
-// the streaming pass kernels (n >= 13).
+// 2302.10083, Algorithm 3, Section 4.1).  Jobs with n <= 14 go to batched
+// launches (whole functions in shared memory, the launch shapes of the batch
+// driver's table); larger jobs run the streaming pass kernels on a stream of
+// their own.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -27,7 +28,7 @@ namespace {
 
 constexpr uint64_t kNone = ~0ull;
 constexpr uint64_t kGrain = 256;
-constexpr int kSmallMaxN = kMaxSmemGroup + kChunkDigits;   // 12: the whole state in one CTA
+constexpr int kSmallMaxN = kFnMaxN;      // 14: the whole state in shared memory (3 CTAs for 14)
 constexpr size_t kMaxBatch = 4096;                        // small jobs per batched launch
 
 uint64_t now_ns()
@@ -405,7 +406,7 @@ void dqmc_server::exec(Group *g)
             b.arena = d_base;
             b.bitmaps = d_base;
             b.count = reinterpret_cast<unsigned long long *>(dp + g->cnt_at);
-            e = launch_sweep(make_plan((int)n), nullptr, nullptr, nullptr, nullptr, nullptr, s, 0, -1, &b);
+            e = launch_batch_in_smem((int)n, b, s);
             i = m;
         }
         if (e == cudaSuccess)

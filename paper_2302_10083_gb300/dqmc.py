@@ -69,6 +69,10 @@ _SIGS = {
     "dqmc_batch_run": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p, c_vp]),
     "dqmc_batch_workspace_bytes": (ctypes.c_uint64, [ctypes.c_uint32, c_u32p]),
     "dqmc_batch_release": (ctypes.c_int, []),
+    "dqmc_batch_get_config": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32 * 5)]),
+    "dqmc_batch_set_config": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32 * 5)]),
+    "dqmc_batch_autotune": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p,
+                                           ctypes.c_uint32, c_vp, ctypes.POINTER(ctypes.c_float)]),
     "dqmc_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(c_vp)]),
     "dqmc_server_destroy": (ctypes.c_int, [c_vp]),
     "dqmc_server_job_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int]),
@@ -327,6 +331,56 @@ def dqmc_batch_run(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, str
 
 def dqmc_batch_release() -> int:
     return lib().dqmc_batch_release()
+
+
+DQMC_BATCH_PATH_SMEM = 0
+DQMC_BATCH_PATH_TILES = 1
+_CFG_KEYS = ("path", "threads_per_fn", "fns_per_cta", "digits_per_step", "ctas_per_fn")
+
+
+def dqmc_batch_get_config(n: int) -> dict:
+    """The launch configuration (dqmc_batch_config) used for functions of n variables."""
+    buf = (ctypes.c_uint32 * 5)()
+    st = lib().dqmc_batch_get_config(n, ctypes.byref(buf))
+    if st != DQMC_OK:
+        raise DqmcError(st, "dqmc_batch_get_config")
+    return dict(zip(_CFG_KEYS, (int(x) for x in buf)))
+
+
+def dqmc_batch_set_config(n: int, cfg: dict) -> int:
+    """Set one n's configuration (keys of dqmc_batch_get_config); returns the status."""
+    buf = (ctypes.c_uint32 * 5)(*(int(cfg.get(k, 1)) for k in _CFG_KEYS))
+    return lib().dqmc_batch_set_config(n, ctypes.byref(buf))
+
+
+def dqmc_batch_autotune(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, stream, reps=3):
+    """dqmc_batch_autotune on a batch (arguments as dqmc_batch_run).  Returns
+    {n: best ms} for the n's present; raises DqmcError on failure."""
+    n_a, n_p = _host_u32(ns)
+    tt_a, tt_p = _host_u64(tt_off)
+    bm_a, bm_p = _host_u64(bm_off)
+    if dc_off is None:
+        dc_a, dc_p = None, None
+    else:
+        dc_a, dc_p = _host_u64(dc_off)
+    out = (ctypes.c_float * (DQMC_BATCH_MAX_N + 1))()
+    st = lib().dqmc_batch_autotune(len(n_a), n_p, tt_p, d_arena, dc_p, d_counts, d_bitmaps, bm_p, reps, stream, out)
+    if st != DQMC_OK:
+        raise DqmcError(st, "dqmc_batch_autotune")
+    return {n: float(out[n]) for n in range(DQMC_BATCH_MAX_N + 1) if out[n] >= 0}
+
+
+def batch_tuning_table() -> dict:
+    """Every n's configuration, keyed by n as a string (the JSON form)."""
+    return {str(n): dqmc_batch_get_config(n) for n in range(DQMC_BATCH_MAX_N + 1)}
+
+
+def load_batch_tuning(table: dict) -> None:
+    """Apply a table from batch_tuning_table (for instance read back from JSON)."""
+    for k, cfg in table.items():
+        st = dqmc_batch_set_config(int(k), cfg)
+        if st != DQMC_OK:
+            raise DqmcError(st, f"dqmc_batch_set_config({k})")
 
 
 # ------------------------------------------------------------------ serving

@@ -3,7 +3,9 @@ headers declare, rejects bad arguments without touching the GPU, and its pass
 plan is sound (every digit merged once and reduced once, tiles cover the rows
 they must, and the grouped schedule gives the oracle's primes when simulated
 on the host)."""
+import ctypes
 import glob
+import json
 import os
 import re
 
@@ -91,10 +93,22 @@ def test_batch_arguments_rejected_without_gpu():
 
 
 def test_batch_workspace_and_layout():
-    # n <= 12 functions need no state; n = 13, 14 one padded state each
-    assert dqmc.dqmc_batch_workspace_bytes(np.array([4, 12])) < 1 << 16
-    w = dqmc.dqmc_batch_workspace_bytes(np.array([13, 14, 14]))
-    assert w >= (3 ** 8 + 2 * 3 ** 9) * 32
+    # n <= 12 functions need no state; on the tile path n = 13, 14 one padded
+    # state each, on the shared-memory path none
+    saved = dqmc.batch_tuning_table()
+    try:
+        assert dqmc.dqmc_batch_workspace_bytes(np.array([4, 12])) < 1 << 16
+        for n in (13, 14):
+            assert dqmc.dqmc_batch_set_config(n, dict(saved[str(n)], path=dqmc.DQMC_BATCH_PATH_TILES)) == 0
+        w = dqmc.dqmc_batch_workspace_bytes(np.array([13, 14, 14]))
+        assert w >= (3 ** 8 + 2 * 3 ** 9) * 32
+        for n in (13, 14):
+            cfg = dict(path=dqmc.DQMC_BATCH_PATH_SMEM, threads_per_fn=256, fns_per_cta=1, digits_per_step=2,
+                       ctas_per_fn=3 if n == 14 else 1)
+            assert dqmc.dqmc_batch_set_config(n, cfg) == 0
+        assert dqmc.dqmc_batch_workspace_bytes(np.array([13, 14, 14])) < 1 << 16
+    finally:
+        dqmc.load_batch_tuning(saved)
     assert dqmc.dqmc_batch_workspace_bytes(np.array([15])) == 0
     off, total = dqmc.batch_bitmap_layout([0, 4, 5, 14])
     sizes = [dqmc.dqmc_bitmap_alloc_bytes(n) for n in (0, 4, 5, 14)]
@@ -116,12 +130,15 @@ def test_server_arguments_rejected_without_gpu():
 
 
 def test_server_job_bytes():
-    # a job holds its truth table(s), its bitmap slot and (n >= 13) its workspace
-    for n in (0, 5, 12, 13, 18, 22):
+    # a job holds its truth table(s), its bitmap slot and (n >= 15, the
+    # streaming path) its workspace; n <= 14 keep their state in shared memory
+    for n in (0, 5, 12, 13, 14, 15, 18, 22):
         b = dqmc.dqmc_server_job_bytes(n)
         assert b >= dqmc.dqmc_bitmap_alloc_bytes(n) + ((1 << n) + 7) // 8
-        if n >= 13:
+        if n >= 15:
             assert b >= dqmc.dqmc_workspace_bytes(n)
+        else:
+            assert b < dqmc.dqmc_bitmap_alloc_bytes(n) + 2 * ((1 << n) + 7) // 8 + 4096
         assert dqmc.dqmc_server_job_bytes(n, True) > b
     assert dqmc.dqmc_server_job_bytes(26) == 0
 
@@ -392,3 +409,65 @@ def test_plan_schedule_simulated(n, seed):
                 S = grouped_reduce(S, n, red)
     want = oracle.sweep(n, on, dc) != 0
     assert np.array_equal(S, want)
+
+
+def _cfg(path, tg, fpc, d, ctas=1):
+    return dict(path=path, threads_per_fn=tg, fns_per_cta=fpc, digits_per_step=d, ctas_per_fn=ctas)
+
+
+def test_batch_config_rules_without_gpu():
+    """dqmc_batch_set_config accepts exactly the launchable shapes (host
+    logic only: threads, functions per CTA, digits per step, shared memory,
+    clusters of 3 for n = 13, 14 and of 9 for n = 14, the shared-memory path
+    only for 5 <= n <= 14)."""
+    saved = dqmc.batch_tuning_table()
+    S, T = dqmc.DQMC_BATCH_PATH_SMEM, dqmc.DQMC_BATCH_PATH_TILES
+    try:
+        for n in range(dqmc.DQMC_BATCH_MAX_N + 1):
+            c = saved[str(n)]
+            assert c["path"] in (S, T) and (c["path"] == T or 5 <= n <= 14)
+            assert dqmc.dqmc_batch_set_config(n, _cfg(T, 0, 0, 0, 0)) == dqmc.DQMC_OK
+        ok = [(5, 32, 15, 2), (5, 32, 8, 3), (12, 512, 1, 3), (12, 64, 3, 2), (13, 1024, 1, 2), (12, 1024, 1, 3),
+              (14, 512, 1, 3, 3), (14, 32, 1, 2, 9), (14, 1024, 1, 3, 9), (13, 256, 1, 2, 3), (10, 96, 3, 3)]
+        bad = [(4, 32, 1, 2),        # below the chunk size
+               (15, 32, 1, 2),       # above the batch range
+               (8, 48, 1, 2),        # not whole warps
+               (8, 0, 1, 2), (8, 32, 0, 2), (8, 32, 16, 2),
+               (8, 64, 1, 4), (8, 64, 1, 1),     # digits per step
+               (8, 512, 4, 2),       # 2048 threads
+               (12, 64, 4, 2),       # 4 x 70 KB of shared memory
+               (13, 64, 2, 2),       # 2 x 210 KB
+               (14, 64, 1, 2),       # 630 KB in one CTA
+               (14, 64, 2, 2, 3),    # clusters hold one function
+               (13, 64, 1, 2, 9),    # nine CTAs only for n = 14
+               (12, 64, 1, 2, 3),    # clusters only for n = 13, 14
+               (14, 64, 1, 2, 2),    # 1, 3 or 9 CTAs
+               (14, 64, 1, 2, 0)]
+        for t in ok:
+            assert dqmc.dqmc_batch_set_config(t[0], _cfg(S, *t[1:])) == dqmc.DQMC_OK, t
+            assert dqmc.dqmc_batch_get_config(t[0]) == _cfg(S, *t[1:])
+        for t in bad:
+            assert dqmc.dqmc_batch_set_config(t[0], _cfg(S, *t[1:])) == dqmc.DQMC_EINVAL, t
+        assert dqmc.dqmc_batch_set_config(2, _cfg(7, 32, 1, 2)) == dqmc.DQMC_EINVAL   # unknown path
+        with pytest.raises(dqmc.DqmcError):
+            dqmc.dqmc_batch_get_config(15)
+        # the JSON form goes through unchanged
+        table = json.loads(json.dumps(dqmc.batch_tuning_table()))
+        dqmc.load_batch_tuning(saved)
+        dqmc.load_batch_tuning(table)
+        assert dqmc.batch_tuning_table() == table
+    finally:
+        dqmc.load_batch_tuning(saved)
+
+
+def test_batch_autotune_arguments_without_gpu():
+    L = dqmc.lib()
+    out = (ctypes.c_float * (dqmc.DQMC_BATCH_MAX_N + 1))()
+    assert L.dqmc_batch_autotune(0, None, None, None, None, None, None, None, 3, None, out) == dqmc.DQMC_OK
+    assert all(x == -1.0 for x in out)
+    n = np.array([5, 6], dtype=np.uint32)
+    o = np.zeros(2, dtype=np.uint64)
+    n_p, o_p = n.ctypes.data_as(dqmc.c_u32p), o.ctypes.data_as(dqmc.c_u64p)
+    assert L.dqmc_batch_autotune(2, n_p, o_p, 256, None, 256, 256, o_p, 0, None, out) == dqmc.DQMC_EINVAL
+    assert L.dqmc_batch_autotune(2, n_p, o_p, 256, None, 256, 256, o_p, 1001, None, out) == dqmc.DQMC_EINVAL
+    assert L.dqmc_batch_autotune(2, None, o_p, 256, None, 256, 256, o_p, 3, None, out) == dqmc.DQMC_EINVAL

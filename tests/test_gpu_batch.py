@@ -1,7 +1,9 @@
 """Batched sweep (dqmc_batch_run) on the GPU: every function of a batch is
-bit-exact against the oracle (bitmap, tail bytes of its slot, count), the
-captured graph gives the same result when launched again, and a new set of
-buffers or functions is captured anew."""
+bit-exact against the oracle (bitmap, tail bytes of its slot, count) on both
+paths (whole functions in shared memory, and the tile / streaming kernels) and
+for every launch shape the autotuner may pick; the captured graph gives the
+same result when launched again, and a new set of buffers, functions or
+configurations is captured anew."""
 import numpy as np
 import pytest
 
@@ -18,8 +20,27 @@ def _gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dqmc.lib()
+    saved = dqmc.batch_tuning_table()
     yield
+    dqmc.load_batch_tuning(saved)
     dqmc.dqmc_batch_release()
+
+
+@pytest.fixture
+def table():
+    """Restores the configuration table after the test."""
+    saved = dqmc.batch_tuning_table()
+    yield saved
+    dqmc.load_batch_tuning(saved)
+
+
+def set_all(path, **shape):
+    for n in range(dqmc.DQMC_BATCH_MAX_N + 1):
+        if path == dqmc.DQMC_BATCH_PATH_TILES or n >= 5:
+            cfg = dict(path=path, threads_per_fn=256, fns_per_cta=1, digits_per_step=2,
+                       ctas_per_fn=3 if n == 14 else 1)
+            cfg.update(shape)
+            assert dqmc.dqmc_batch_set_config(n, cfg) == dqmc.DQMC_OK
 
 
 def run_batch(b, with_dc=True):
@@ -109,3 +130,95 @@ def test_batch_matches_single_function_calls():
         single = dqmc.dqmc_primes(n, on, dc)
         o = int(bm_off[f])
         assert np.array_equal(bm[o: o + len(single)], single)
+
+
+@pytest.mark.parametrize("path", ["tiles", "smem"])
+def test_batch_each_path_bit_exact(path, table):
+    """The whole mixed batch on one path: the tile / streaming kernels for
+    every n, or shared memory for every n >= 5."""
+    if path == "tiles":
+        set_all(dqmc.DQMC_BATCH_PATH_TILES)
+    else:
+        set_all(dqmc.DQMC_BATCH_PATH_SMEM, threads_per_fn=256, digits_per_step=3)
+    b = synth.batch_functions(count=120, seed=11)
+    arena, bitmaps, counts, bm_off, dc_off = run_batch(b)
+    check_batch(b, bitmaps, counts, bm_off, dc_off)
+
+
+# (n, threads per function, functions per CTA, digits per step, CTAs per
+# function): every n of the shared-memory path, both step sizes, one warp up
+# to 1024 threads, clusters of 3 and 9, and CTAs whose last functions are
+# missing (13 functions per batch).
+SMEM_SHAPES = [
+    (5, 32, 8, 2, 1), (5, 64, 3, 3, 1), (6, 32, 6, 3, 1), (7, 32, 4, 2, 1), (8, 64, 4, 3, 1), (8, 32, 15, 2, 1),
+    (9, 128, 2, 2, 1), (9, 32, 1, 3, 1), (10, 96, 3, 3, 1), (10, 1024, 1, 2, 1), (11, 256, 2, 2, 1),
+    (11, 32, 1, 3, 1), (12, 512, 1, 3, 1), (12, 128, 3, 2, 1), (12, 1024, 1, 3, 1), (13, 512, 1, 3, 1),
+    (13, 1024, 1, 2, 1), (13, 64, 1, 2, 1), (13, 256, 1, 3, 3), (13, 1024, 1, 2, 3), (14, 512, 1, 3, 3),
+    (14, 1024, 1, 2, 3), (14, 128, 1, 3, 3), (14, 256, 1, 3, 9), (14, 1024, 1, 2, 9), (14, 64, 1, 3, 9),
+]
+
+
+@pytest.mark.parametrize("n,tg,fpc,d,ctas", SMEM_SHAPES)
+def test_batch_smem_shapes_bit_exact(n, tg, fpc, d, ctas, table):
+    cfg = dict(path=dqmc.DQMC_BATCH_PATH_SMEM, threads_per_fn=tg, fns_per_cta=fpc, digits_per_step=d,
+               ctas_per_fn=ctas)
+    assert dqmc.dqmc_batch_set_config(n, cfg) == dqmc.DQMC_OK
+    b = synth.batch_functions(count=13, seed=100 + n, n_lo=n, n_hi=n)
+    arena, bitmaps, counts, bm_off, dc_off = run_batch(b)
+    check_batch(b, bitmaps, counts, bm_off, dc_off)
+
+
+def test_batch_smem_constant_and_parity_functions(table):
+    """Closed forms through the shared-memory path: constant 1 (only the
+    all-'*' cube), constant 0 (no primes) and parity (its 2^(n-1) minterms),
+    for n = 5, 9, 13 and 14."""
+    set_all(dqmc.DQMC_BATCH_PATH_SMEM, threads_per_fn=256, digits_per_step=3)
+    ns, tabs = [], []
+    for n in (5, 9, 13, 14):
+        nb = (1 << n) // 8
+        x = np.arange(1 << n)
+        par = np.packbits((np.unpackbits(x.astype(">u4").view(np.uint8)).reshape(-1, 32).sum(1) & 1).astype(np.uint8),
+                          bitorder="little")
+        for t in (np.full(nb, 0xFF, np.uint8), np.zeros(nb, np.uint8), par):
+            ns.append(n)
+            tabs.append(t)
+    off, pos, parts = [], 0, []
+    for t in tabs:
+        off.append(pos)
+        parts.append(t)
+        pos += len(t)
+    b = {"n": np.array(ns), "tt_off": np.array(off, np.uint64), "arena": np.concatenate(parts),
+         "dc_off": np.full(len(ns), np.iinfo(np.uint64).max, np.uint64)}
+    arena, bitmaps, counts, bm_off, _ = run_batch(b, with_dc=False)
+    cnt = counts.cpu().numpy()
+    bm = bitmaps.cpu().numpy()
+    for f, n in enumerate(ns):
+        kind = f % 3
+        want = [1, 0, 1 << (n - 1)][kind]
+        assert int(cnt[f]) == want, (n, kind)
+        bits = np.unpackbits(bm[int(bm_off[f]): int(bm_off[f]) + (3 ** n + 7) // 8], bitorder="little")[: 3 ** n]
+        if kind == 0:
+            assert bits[3 ** n - 1] == 1   # the all-'*' cube: every digit 2
+    check_batch(b, bitmaps, counts, bm_off, None)
+
+
+def test_autotune_then_run_bit_exact(table):
+    """The autotuner picks a launchable configuration for every n present,
+    reports a time for each, and the batch run with its choices is exact."""
+    b = synth.batch_functions(count=200, seed=21)
+    ns = b["n"].astype(np.uint32)
+    dev = "cuda:0"
+    arena = torch.from_numpy(b["arena"]).to(dev)
+    bm_off, total = dqmc.batch_bitmap_layout(ns)
+    bitmaps = torch.zeros(total, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(len(ns), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    best = dqmc.dqmc_batch_autotune(ns, b["tt_off"], arena.data_ptr(), b["dc_off"], counts.data_ptr(),
+                                    bitmaps.data_ptr(), bm_off, stream, reps=1)
+    assert sorted(best) == sorted(set(int(n) for n in ns)) and all(ms > 0 for ms in best.values())
+    for n in best:
+        c = dqmc.dqmc_batch_get_config(n)
+        assert c["path"] in (dqmc.DQMC_BATCH_PATH_SMEM, dqmc.DQMC_BATCH_PATH_TILES)
+        assert dqmc.dqmc_batch_set_config(n, c) == dqmc.DQMC_OK
+    _, bitmaps, counts, bm_off, dc_off = run_batch(b)
+    check_batch(b, bitmaps, counts, bm_off, dc_off)
