@@ -34,18 +34,31 @@ struct ClassConfig {
     FnConfig fn;
 };
 
-ClassConfig default_config(int n)
+// Shared-memory shape of one n: threads per function, functions per CTA,
+// digits per step, CTAs per function (measured best on a GB300 for 5958
+// functions of that n; n = 14 on a cluster of nine).
+ClassConfig smem_config(int n)
 {
     ClassConfig c;
-    if (n < kFnMinN) return c;
+    if (n < kFnMinN || n > kFnMaxN) return c;
+    static const int tg[kClasses] = {0, 0, 0, 0, 0, 32, 32, 32, 32, 32, 32, 64, 256, 1024, 256};
+    static const int fpc[kClasses] = {0, 0, 0, 0, 0, 4, 8, 8, 8, 8, 8, 2, 1, 1, 1};
+    static const int dig[kClasses] = {0, 0, 0, 0, 0, 2, 3, 2, 2, 2, 3, 3, 3, 3, 3};
     c.path = DQMC_BATCH_PATH_SMEM;
-    static const int tg[kClasses] = {0, 0, 0, 0, 0, 32, 32, 32, 32, 32, 32, 64, 256, 512, 512};
-    static const int fpc[kClasses] = {0, 0, 0, 0, 0, 8, 8, 8, 8, 8, 8, 2, 1, 1, 1};
     c.fn.tg = tg[n];
     c.fn.fpc = fpc[n];
-    c.fn.digits = 3;
-    c.fn.ctas = n == 14 ? 3 : 1;
+    c.fn.digits = dig[n];
+    c.fn.ctas = n == 14 ? 9 : 1;
     return c;
+}
+
+// Built-in table (the autotuner's choices on the 65,536-function batch on a
+// GB300): shared memory for 5 <= n <= 13, the streaming kernels for n = 14
+// (4.3 ms against 5.3 ms for the nine-CTA clusters) and the tile kernel below 5.
+ClassConfig default_config(int n)
+{
+    if (n < kFnMinN || n == 14) return ClassConfig{};
+    return smem_config(n);
 }
 
 std::mutex g_cfg_mu;
@@ -267,7 +280,7 @@ cudaError_t launch_batch_in_smem(int n, const BatchArgs &b, cudaStream_t s)
     if (n < kFnMinN) return launch_sweep(make_plan(n), nullptr, nullptr, nullptr, nullptr, nullptr, s, 0, -1, &b);
     ClassConfig cfg[kClasses];
     config_snapshot(cfg, nullptr);
-    const ClassConfig cc = cfg[n].path == DQMC_BATCH_PATH_SMEM ? cfg[n] : default_config(n);
+    const ClassConfig cc = cfg[n].path == DQMC_BATCH_PATH_SMEM ? cfg[n] : smem_config(n);
     return launch_fn_batch(n, b, cc.fn, s);
 }
 

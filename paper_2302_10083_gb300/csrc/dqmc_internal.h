@@ -192,8 +192,9 @@ bool fn_config_ok(int n, const FnConfig &c);
 cudaError_t launch_fn_batch(int n, const BatchArgs &b, const FnConfig &c, cudaStream_t s);
 
 // Sweep a batch of functions of one n <= 14 without device state: the
-// shared-memory kernel with the batch table's shape for n (its default
-// shape if the table says the tile path), the one-tile kernel below n = 5.
+// shared-memory kernel with the batch table's shape for n (the built-in
+// shared-memory shape if the table says the tile path), the one-tile kernel
+// below n = 5.
 cudaError_t launch_batch_in_smem(int n, const BatchArgs &b, cudaStream_t s);
 
 // Enqueue compaction of a dense bitmap into (mask, value) pairs.

@@ -427,8 +427,11 @@ std::vector<Group *> dqmc_server::admit()
     std::vector<Group *> out;
     if (sticky) return out;
     if (mode == DQMC_SERVER_SERIAL) {
+        // one job at a time, on the same kernels as the concurrent mode: a
+        // small job is a batch of one (its footprint has no workspace)
         if (running_groups || queue.empty()) return out;
-        Group *g = prepare_single(queue.front(), 0);
+        const uint64_t id = queue.front();
+        Group *g = (int)jobs[id].n <= kSmallMaxN ? prepare_batch(std::vector<uint64_t>{id}) : prepare_single(id, 0);
         if (g) {
             queue.pop_front();
             out.push_back(g);

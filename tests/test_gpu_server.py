@@ -102,3 +102,21 @@ def test_replay_counts_match_alone():
     assert span > 0 and (lat >= 0).all()
     for (n, on, dc), c in zip(jobs, counts):
         assert int(c) == dqmc.dqmc_count(n, on, dc)
+
+
+@pytest.mark.parametrize("mode", ["concurrent", "serial"])
+def test_shared_memory_sizes_in_both_modes(mode):
+    """Jobs of n = 13 and 14 (batched on the shared-memory path, no
+    workspace in their footprint) next to small and large jobs, in either
+    mode: each bitmap equals the function swept alone."""
+    jobs = []
+    for j, n in enumerate([13, 14, 8, 15, 14, 13, 6, 14]):
+        on, dc = synth.random_function(n, 300 + j, 0.6 + 0.04 * j, 0.05 if j % 2 else 0.0)
+        jobs.append((n, on, dc))
+    m = dqmc.DQMC_SERVER_SERIAL if mode == "serial" else dqmc.DQMC_SERVER_CONCURRENT
+    with dqmc.Server(2 << 30, streams=1 if mode == "serial" else 4, mode=m) as srv:
+        got = run_mix(srv, jobs)
+    for (n, on, dc), (cnt, bm) in zip(jobs, got):
+        alone = dqmc.dqmc_primes(n, on, dc)
+        assert np.array_equal(bm, alone), f"n={n}"
+        assert cnt == int(np.unpackbits(alone).sum())
