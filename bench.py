@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--serve-jobs", type=int, default=2000, help="serving: jobs per arrival rate at most")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving: arrival span per rate at most")
     ap.add_argument("--batch", type=int, default=65536, help="functions in the batched workload")
+    ap.add_argument("--no-one-by-one", action="store_true",
+                    help="batched: skip the one-launch-per-function comparison (for profiling the graph alone)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched: keep the built-in launch table instead of tuning it on the batch first")
     return ap.parse_args()
@@ -430,6 +432,10 @@ def run_batched(args, rank, world, local):
     bm_graph = bitmaps.clone()
     cnt_graph = counts.clone()
 
+    if args.no_one_by_one:
+        return report_batched(args, rank, world, b, nf, ns, total, ms, clocks, None, None, True, tune_s, tune_ms,
+                              table, None)
+
     # one launch sequence per function (dqmc_primes_dev), same buffers
     work_bytes = max(dqmc.dqmc_workspace_bytes(int(n)) for n in set(ns.tolist()))
     work = torch.empty(work_bytes, dtype=torch.uint8, device=dev)
@@ -459,16 +465,24 @@ def run_batched(args, rank, world, local):
         raise SystemExit("batched and one-by-one results differ")
 
     # end to end: truth tables in from pinned host memory, counts out
-    counts_h = torch.empty(nf, dtype=torch.int64).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(K):
-        arena.copy_(arena_h, non_blocking=True)
-        graph_run()
-        counts_h.copy_(counts, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / K
+    e2e_s = None
+    if not args.no_e2e:
+        counts_h = torch.empty(nf, dtype=torch.int64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            arena.copy_(arena_h, non_blocking=True)
+            graph_run()
+            counts_h.copy_(counts, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / K
+    return report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, same, False, tune_s, tune_ms,
+                          table, e2e_s)
 
+
+def report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, same, skipped, tune_s, tune_ms,
+                   table, e2e_s):
+    K = args.steps
     cubes = int(sum(3 ** int(n) for n in ns))
     value = world * nf / (ms / 1e3)
     result = {
@@ -483,19 +497,33 @@ def run_batched(args, rank, world, local):
                    "l2": "no flush: the bitmaps (%.1f GB) exceed the 129 MB L2" % (total / 1e9),
                    "parallelism": f"replicas x{world}"},
         "cubes_per_s": world * cubes / (ms / 1e3),
-        "one_launch_per_function": {"value": nf / (ms_single / 1e3), "unit": "functions/s",
-                                    "ms_per_step": ms_single, "api": "dqmc_primes_dev, one call per function"},
-        "speedup_vs_one_launch_per_function": ms_single / ms,
+        "one_launch_per_function": None if skipped else {
+            "value": nf / (ms_single / 1e3), "unit": "functions/s", "ms_per_step": ms_single,
+            "api": "dqmc_primes_dev, one call per function"},
+        "speedup_vs_one_launch_per_function": None if skipped else ms_single / ms,
         "results_identical": same,
         "launch_table": {"autotuned": not args.no_autotune, "seconds": tune_s,
                          "best_ms_per_n": tune_ms, "config_per_n": table},
-        "e2e": {"value": world * nf / e2e_s, "unit": "functions/s", "h2d_bytes_per_step": int(b["arena"].size),
-                "d2h_bytes_per_step": 8 * nf},
+        "e2e": None if e2e_s is None else {
+            "value": world * nf / e2e_s, "unit": "functions/s", "h2d_bytes_per_step": int(b["arena"].size),
+            "d2h_bytes_per_step": 8 * nf},
         "clocks": clocks,
+        "gpu_launches": K * launches_per_graph(ns, table),
     }
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
+
+
+def launches_per_graph(ns, table):
+    """Kernels one dqmc_batch_run graph launches: one per n on the shared-memory
+    path and for the one-tile kernel, one per pass on the streaming path."""
+    from paper_2302_10083_gb300 import dqmc
+    k = 0
+    for n in sorted(set(int(x) for x in ns)):
+        cfg = table[str(n)]
+        k += 1 if (cfg["path"] == dqmc.DQMC_BATCH_PATH_SMEM or n <= 12) else dqmc.dqmc_plan_passes(n)
+    return k
 
 
 def run_serving(args, rank, world, local):

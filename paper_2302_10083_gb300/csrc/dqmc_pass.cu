@@ -341,7 +341,6 @@ __device__ unsigned long long lookback_p(const PassParams &P, uint64_t T, bool &
 }
 
 struct PassShared {
-    alignas(8) unsigned char fix_raw[sizeof(FixedDigits)];  // FixedDigits, copied from the parameters
     uint64_t base, ttb, tile;
     uint64_t bar;                         // mbarrier of the tile's bulk loads
     unsigned long long excl;
@@ -351,45 +350,62 @@ struct PassShared {
     int list_ok, overflow, next_region, load_fail;
     uint16_t c5[243];                     // copy of the chunk-cell table
     uint16_t code[kUnits];                // copy of the unit-digit table
-    __device__ const FixedDigits &fix() const { return *reinterpret_cast<const FixedDigits *>(fix_raw); }
 };
 
-// Tile id -> first state row (S.base) and first truth-table word (S.ttb).
-// With kTicket and a list, tiles take ids in the order they start, so a
-// tile's look-back waits only on tiles already running.
+// Tile id -> first state row (S.base), first truth-table word (S.ttb) and
+// the literal / value bits of the digits fixed per tile (S.tile_mask / val,
+// bit 5 + j for high digit j).  Thread 0 only, reading the fixed-digit table
+// from the kernel parameters; the caller's next barrier publishes S.  With
+// kTicket and a list, tiles take ids in the order they start, so a tile's
+// look-back waits only on tiles already running.
 template <bool kTicket>
-__device__ __forceinline__ void decode_tile(const PassParams &P, PassShared &S, uint64_t tile)
+__device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S, uint64_t tile)
 {
-    const int tid = threadIdx.x;
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(&P.fix);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(S.fix_raw);
-        for (int i = tid; i < (int)(sizeof(FixedDigits) / 4); i += (int)blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const FixedDigits &f = S.fix();
-        uint64_t t = tile;
-        if (kTicket && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
-        uint64_t base = 0, ttb = 0, x = t;
+    const FixedDigits &f = P.fix;
+    uint64_t t = tile;
+    if (kTicket && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
+    uint64_t base = 0, ttb = 0;
+    uint32_t m = 0, vv = 0;
+    auto put = [&](int i, uint32_t d) {
+        base += d * f.w3[i];
+        ttb += d * f.w2[i];
+        if (d != 2) m |= 1u << (kChunkDigits + f.j[i]);
+        if (d == 1) vv |= 1u << (kChunkDigits + f.j[i]);
+    };
+    if (t >> 32) {
+        uint64_t x = t;
         for (int i = 0; i < f.n; ++i) {
-            uint64_t d;
+            uint32_t d;
+            if (f.r[i] == 2) {
+                d = (uint32_t)(x & 1u);
+                x >>= 1;
+            } else {
+                const uint64_t q = x / 3u;
+                d = (uint32_t)(x - 3u * q);
+                x = q;
+            }
+            put(i, d);
+        }
+    } else {
+        uint32_t x = (uint32_t)t;   // the usual case: 32-bit division by 3
+        for (int i = 0; i < f.n; ++i) {
+            uint32_t d;
             if (f.r[i] == 2) {
                 d = x & 1u;
                 x >>= 1;
             } else {
-                const uint64_t q = x / 3u;
+                const uint32_t q = x / 3u;
                 d = x - 3u * q;
                 x = q;
             }
-            base += d * f.w3[i];
-            ttb += d * f.w2[i];
+            put(i, d);
         }
-        S.base = base;
-        S.ttb = ttb;
-        S.tile = t;
     }
-    __syncthreads();
+    S.base = base;
+    S.ttb = ttb;
+    S.tile = t;
+    S.tile_mask = m;
+    S.tile_val = vv;
 }
 
 // ------------------------------------------------------------ first pass
@@ -402,7 +418,8 @@ __global__ void __launch_bounds__(kThreads, 3) tt_pass_kernel(const __grid_const
     __shared__ PassShared S;
     const int tid = threadIdx.x;
     const FnBufs F = fn_bufs(P);
-    decode_tile<false>(P, S, F.tile);
+    if (tid == 0) decode_tile0<false>(P, S, F.tile);
+    __syncthreads();
     const uint64_t base = S.base, ttb = S.ttb;
 
     for (int gb = tid; gb < (1 << kTileDigits); gb += kThreads) {
@@ -532,26 +549,22 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
     const FnBufs F = fn_bufs(P);
-    decode_tile<MODE == kModeOut>(P, S, F.tile);
-    for (int i = tid; i < kUnits; i += NT) S.code[i] = g_tab.code[i];
-    if constexpr (MODE == kModeOut) {
-        for (int i = tid; i < 243; i += NT) S.c5[i] = g_tab.c5[i];
-        if (tid == 0) {
-            S.overflow = 0;
-            // literal / value bits of the high digits >= 7 (fixed in this tile)
-            uint64_t xt = S.tile;
-            uint32_t m = 0, vv = 0;
-            for (int d = kTileDigits; d < P.H; ++d) {
-                const uint64_t q = xt / 3u;
-                const uint32_t dg = (uint32_t)(xt - 3u * q);
-                xt = q;
-                if (dg != 2) m |= 1u << (kChunkDigits + d);
-                if (dg == 1) vv |= 1u << (kChunkDigits + d);
-            }
-            S.tile_mask = m;
-            S.tile_val = vv;
+    if (tid == 0) {
+        decode_tile0<MODE == kModeOut>(P, S, F.tile);
+        S.overflow = 0;
+        if constexpr (B == 0) {
+            S.load_fail = 0;
+            mbar_init(&S.bar, 1);
+            mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
         }
     }
+    __syncthreads();
+    // the unit tables are copied while the tile's loads are in flight (below)
+    auto fill_tables = [&]() {
+        for (int i = tid; i < kUnits; i += NT) S.code[i] = g_tab.code[i];
+        if constexpr (MODE == kModeOut)
+            for (int i = tid; i < 243; i += NT) S.c5[i] = g_tab.c5[i];
+    };
     const uint64_t base = S.base;
     const uint64_t w_g = P.w_g;
     uint4 *const state = F.state;
@@ -573,12 +586,6 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
     // mbarrier whose wait is bounded.  Other tiles are 96-byte runs far apart:
     // cp.async of 16-byte pieces, consecutive lanes on consecutive pieces.
     if constexpr (B == 0) {
-        if (tid == 0) {
-            S.load_fail = 0;
-            mbar_init(&S.bar, 1);
-            mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
-        }
-        __syncthreads();
         for (int q = 4 * tid; q < kUnits; q += 4 * NT) {
             const int nu = min(4, kUnits - q);
             const uint64_t row0 = unit_row(q);
@@ -587,6 +594,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
             bulk_g2s(&tile[uslot(q, 0)], &state[2 * row0], 96u * (uint32_t)nu, &S.bar);
         }
         if (tid < 6) tile[kZeroSlot + tid] = make_uint4(0u, 0u, 0u, 0u);
+        fill_tables();
         const uint64_t t0 = globaltimer_p();
         while (!mbar_try_wait(&S.bar, 0)) {
             if (globaltimer_p() - t0 > P.wait_ns) {
@@ -622,6 +630,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
             cp_async16p(&tile[uslot(u, c)], &state[2 * row0 + c]);
         }
         if (tid < 6) tile[kZeroSlot + tid] = make_uint4(0u, 0u, 0u, 0u);
+        fill_tables();
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
     }
