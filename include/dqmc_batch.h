@@ -13,7 +13,10 @@
  *       CTA, threads_per_fn threads each, the high digits merged and reduced
  *       digits_per_step at a time; or one function per cluster of
  *       ctas_per_fn = 3 (n = 13, 14) or 9 (n = 14) CTAs, the top one or two
- *       high digits spread over the cluster (distributed shared memory);
+ *       high digits spread over the cluster (distributed shared memory); for
+ *       n = 14, ctas_per_fn = 1 is one CTA per SM taking functions in turn
+ *       and their three top-digit thirds one after the other (the '*' third
+ *       parked in a workspace slot);
  *   DQMC_BATCH_PATH_TILES  n <= 12: one CTA per function (the kernel of the
  *       single-function sweep); n = 13, 14: the streaming pass kernels, one
  *       launch per pass for all functions of that n, each function with its
@@ -47,9 +50,11 @@ extern "C" {
  * 5 <= n <= 14, threads_per_fn a multiple of 32 (>= 32),
  * 1 <= fns_per_cta <= 15, digits_per_step 2 or 3,
  * threads_per_fn * fns_per_cta <= 1024, ctas_per_fn 1, 3 (n = 13, 14) or
- * 9 (n = 14) with fns_per_cta = 1 when it is above 1, and
+ * 9 (n = 14) with fns_per_cta = 1 when it is above 1 or n = 14, and
  * fns_per_cta * 3^(n-5-c) * 32 bytes of shared memory per CTA <= 227 KB,
- * c = 0, 1, 2 for 1, 3, 9 CTAs per function. */
+ * c = 0, 1, 2 for 1, 3, 9 CTAs per function (c = 1 for n = 14 on one CTA).
+ * The server (dqmc_server.h) runs n = 14 on nine-CTA clusters when the
+ * table says one CTA. */
 typedef struct {
     uint32_t path;
     uint32_t threads_per_fn;   /* threads per function (per CTA of a cluster) */

@@ -34,16 +34,17 @@ struct ClassConfig {
     FnConfig fn;
 };
 
-// Shared-memory shape of one n: threads per function, functions per CTA,
-// digits per step, CTAs per function (measured best on a GB300 for 5958
-// functions of that n; n = 14 on a cluster of nine).
+// Shared-memory shape of one n that needs no scratch (the server's): threads
+// per function, functions per CTA, digits per step, CTAs per function
+// (measured best on a GB300 for 5958 functions of that n; n = 14 on a
+// cluster of nine).
 ClassConfig smem_config(int n)
 {
     ClassConfig c;
     if (n < kFnMinN || n > kFnMaxN) return c;
-    static const int tg[kClasses] = {0, 0, 0, 0, 0, 32, 32, 32, 32, 32, 32, 64, 256, 1024, 256};
-    static const int fpc[kClasses] = {0, 0, 0, 0, 0, 4, 8, 8, 8, 8, 8, 2, 1, 1, 1};
-    static const int dig[kClasses] = {0, 0, 0, 0, 0, 2, 3, 2, 2, 2, 3, 3, 3, 3, 3};
+    static const int tg[kClasses] = {0, 0, 0, 0, 0, 32, 32, 32, 32, 32, 32, 128, 256, 1024, 256};
+    static const int fpc[kClasses] = {0, 0, 0, 0, 0, 6, 8, 8, 8, 6, 8, 2, 1, 1, 1};
+    static const int dig[kClasses] = {0, 0, 0, 0, 0, 2, 2, 2, 3, 2, 3, 3, 3, 3, 3};
     c.path = DQMC_BATCH_PATH_SMEM;
     c.fn.tg = tg[n];
     c.fn.fpc = fpc[n];
@@ -53,12 +54,18 @@ ClassConfig smem_config(int n)
 }
 
 // Built-in table (the autotuner's choices on the 65,536-function batch on a
-// GB300): shared memory for 5 <= n <= 13, the streaming kernels for n = 14
-// (4.3 ms against 5.3 ms for the nine-CTA clusters) and the tile kernel below 5.
+// GB300): shared memory for 5 <= n <= 14, n = 14 on one CTA per SM doing the
+// thirds of the top digit in turn (3.6 ms against 4.2 ms for the streaming
+// kernels and 5.5 ms for nine-CTA clusters), the tile kernel below n = 5.
 ClassConfig default_config(int n)
 {
-    if (n < kFnMinN || n == 14) return ClassConfig{};
-    return smem_config(n);
+    if (n < kFnMinN) return ClassConfig{};
+    ClassConfig c = smem_config(n);
+    if (n == 14) {
+        c.fn.tg = 1024;
+        c.fn.ctas = 1;
+    }
+    return c;
 }
 
 std::mutex g_cfg_mu;
@@ -102,8 +109,22 @@ struct BatchLayout {
     uint64_t tt_off = 0, dc_off = 0, bm_off = 0;   // uint64 per function id
     uint64_t ctrl_off[kClasses] = {};
     uint64_t state_off[kClasses] = {};
+    uint64_t scratch_off = 0;       // n = 14 in one CTA: a third per CTA slot
+    uint32_t scratch_ctas = 0;
     uint64_t total = 0;
 };
+
+// CTA slots of the one-CTA n = 14 kernel: one per SM (210 KB of shared memory each).
+uint32_t thirds_slots()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return 160;   // no device to ask (workspace sizing on a host without one)
+    }
+    return (uint32_t)sms;
+}
 
 BatchLayout batch_layout(uint32_t nfun, const uint32_t count[kClasses], const ClassConfig cfg[kClasses])
 {
@@ -125,6 +146,11 @@ BatchLayout batch_layout(uint32_t nfun, const uint32_t count[kClasses], const Cl
         at = align_up_b(at + ctrl_layout(p).bytes, 256);
         L.state_off[c] = at;
         at = align_up_b(at + (uint64_t)count[c] * p.state_rows * kChunkBytes, 256);
+    }
+    if (count[14]) {   // reserved whenever n = 14 is present, so that the autotuner can try it
+        L.scratch_ctas = thirds_slots();
+        L.scratch_off = at;
+        at = align_up_b(at + (uint64_t)L.scratch_ctas * kFnThirdBytes, 256);
     }
     L.total = at;
     return L;
@@ -265,6 +291,10 @@ cudaError_t launch_class(BatchCache &c, const BatchLayout &L, int cl, const Clas
     b.arena = static_cast<const uint8_t *>(d_tt_arena);
     b.bitmaps = static_cast<uint8_t *>(d_out_bitmaps);
     b.count = reinterpret_cast<unsigned long long *>(d_out_count);
+    if (L.scratch_ctas) {
+        b.scratch = work + L.scratch_off;
+        b.scratch_ctas = L.scratch_ctas;
+    }
     if (cc.path == DQMC_BATCH_PATH_SMEM) return launch_fn_batch(cl, b, cc.fn, s);
     const Plan p = make_plan(cl);
     if (p.sps.empty()) return launch_sweep(p, nullptr, nullptr, nullptr, nullptr, nullptr, s, 0, -1, &b);
@@ -280,7 +310,9 @@ cudaError_t launch_batch_in_smem(int n, const BatchArgs &b, cudaStream_t s)
     if (n < kFnMinN) return launch_sweep(make_plan(n), nullptr, nullptr, nullptr, nullptr, nullptr, s, 0, -1, &b);
     ClassConfig cfg[kClasses];
     config_snapshot(cfg, nullptr);
-    const ClassConfig cc = cfg[n].path == DQMC_BATCH_PATH_SMEM ? cfg[n] : smem_config(n);
+    // the server has no scratch for the one-CTA n = 14 kernel: clusters there
+    const bool usable = cfg[n].path == DQMC_BATCH_PATH_SMEM && !(n == 14 && cfg[n].fn.ctas == 1);
+    const ClassConfig cc = usable ? cfg[n] : smem_config(n);
     return launch_fn_batch(n, b, cc.fn, s);
 }
 

@@ -28,8 +28,9 @@
 //     higher digits are 0/1 (the others are still empty); Reduce may take the
 //     digits in any order (the grouped form of ReduceAll, see dqmc_sweep.cu).
 //   * The chunk digits are reduced per row in registers with funnel shifts;
-//     each warp packs its 32 rows (243 words) in place, and the bitmap goes
-//     out in coalesced 16-byte stores.
+//     each warp packs its 32 rows (243 words) in place and stores them to the
+//     bitmap at once (coalesced; a cluster's CTAs, whose streams start inside
+//     a word, go through a second phase with masked atomics at the seams).
 #include <cooperative_groups.h>
 
 #include "dqmc_chunk.cuh"
@@ -51,6 +52,7 @@ struct FnArgs {
     uint8_t *bitmaps;
     unsigned long long *count;
     uint64_t out_words, out_alloc_words;   // ceil(3^n / 32), bitmap slot in words
+    uint4 *scratch;                 // n = 14 in one CTA: 3^8 rows per CTA of the grid
 };
 
 // Shared-memory layout of a function's rows: row r at bytes 32r .. 32r+31,
@@ -257,6 +259,141 @@ __device__ __forceinline__ void reduce_all(uint4 *S, int lt, int tg, const SubSy
     }
 }
 
+// Binary rows of one part of a function from its truth table (word g holds
+// the 32 minterms of binary row g), chunk digits merged on the way.  The part
+// holds the cubes whose top CD high digits (above the HL it holds) are the
+// base-3 digits of `part`; word gb + 2^HL b0 + 2^(HL+1) b1 holds binary row gb
+// with those digits (b0, b1), and a '*' digit ANDs both values.
+template <int HL, int CD>
+__device__ __forceinline__ void load_rows(uint4 *S, const uint32_t *on, const uint32_t *dc, int part, int lt, int tg)
+{
+    constexpr int NB = 1 << HL;
+    const int cd0 = CD >= 1 ? part % 3 : 0, cd1 = CD >= 2 ? part / 3 : 0;
+    for (int gb = lt; gb < NB; gb += tg) {
+        uint32_t x = 0xffffffffu;
+#pragma unroll
+        for (int b1 = 0; b1 < (CD >= 2 ? 2 : 1); ++b1) {
+            if (CD >= 2 && cd1 != 2 && b1 != cd1) continue;
+#pragma unroll
+            for (int b0 = 0; b0 < (CD >= 1 ? 2 : 1); ++b0) {
+                if (CD >= 1 && cd0 != 2 && b0 != cd0) continue;
+                const int wi = gb + (b0 << HL) + (b1 << (HL + 1));
+                x &= __ldg(on + wi) | (dc ? __ldg(dc + wi) : 0u);
+            }
+        }
+        uint32_t v[kChunkWords];
+        chunk_merge_from_tt(x, v);
+        st_row(S, spread3k<HL>(gb), v);
+    }
+}
+
+// Chunk digits, count, and the rows packed into the dense stream in place: a
+// warp takes regions of 32 rows (1 KB of shared memory; 32 rows of 243 cells
+// are exactly 243 words), reduces each row's chunk digits in registers and
+// writes the region's packed words to its start.  Lane l's row starts at bit
+// 243 l of the region; the word it shares with the next row is completed by
+// the next lane.  With DIRECT (a stream that starts at bit 0 of `out`) each
+// region also goes to `out` at once.  Returns this thread's count of set cells.
+template <int R, bool DIRECT>
+__device__ __forceinline__ unsigned long long chunk_pack(uint4 *S, uint32_t *out, int lt, int tg)
+{
+    constexpr int C3 = (int)pow3(kChunkDigits);
+    constexpr int NREG = (R + 31) / 32;
+    constexpr int NP = (int)(((uint64_t)R * C3 + 31) / 32);   // packed words
+    const int lane = (int)threadIdx.x & 31, nwarp = tg >> 5;
+    uint32_t *Sw = reinterpret_cast<uint32_t *>(S);
+    unsigned long long bits = 0;
+    const int sh = (C3 * lane) & 31, w0 = (C3 * lane) >> 5;
+    const bool k8 = sh + C3 > 256;                     // the row's last word is word 8 (else 7)
+    const bool shares = ((sh + C3) & 31) != 0;         // the next row starts inside it
+    for (int g = lt >> 5; g < NREG; g += nwarp) {
+        const int r = 32 * g + lane;
+        uint32_t v[kChunkWords];
+        if (r < R) {
+            ld_row(S, r, v);
+            chunk_reduce_row(v);
+        } else {
+#pragma unroll
+            for (int w = 0; w < kChunkWords; ++w) v[w] = 0;
+        }
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w) bits += __popc(v[w]);
+        uint32_t o[kChunkWords + 1];
+        o[0] = __funnelshift_l(0u, v[0], sh);
+#pragma unroll
+        for (int k = 1; k < kChunkWords; ++k) o[k] = __funnelshift_l(v[k - 1], v[k], sh);
+        o[kChunkWords] = __funnelshift_l(v[kChunkWords - 1], 0u, sh);
+        const uint32_t tailw = k8 ? o[8] : o[7];
+        const uint32_t from_prev = __shfl_up_sync(0xffffffffu, tailw, 1);
+        if (lane > 0 && sh != 0) o[0] |= from_prev;
+        __syncwarp();   // every row of the region is in registers before it is overwritten
+        if (r < R) {
+            const bool own_last = !shares || lane == 31 || r + 1 >= R;
+            uint32_t *dst = Sw + 256 * g + w0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) dst[k] = o[k];
+            if (k8 || own_last) dst[7] = o[7];
+            if (k8 && own_last) dst[8] = o[8];
+        }
+        __syncwarp();
+        if constexpr (DIRECT) {
+            const int nwords = (g == NREG - 1) ? NP - C3 * g : C3;
+            const uint32_t *src = Sw + 256 * g;
+            uint32_t *dst = out + C3 * g;
+            for (int k = lane; k < nwords; k += 32) dst[k] = src[k];
+        }
+    }
+    return bits;
+}
+
+// Part `part` of `parts` (rows part*R .. part*R + R-1 of the function) from
+// its packed regions to the bitmap: its stream starts at bit part*R*243, and
+// the words it shares with the neighbouring parts are written with masked
+// atomics.  The last part also zeroes the slot past the stream.
+template <int R>
+__device__ __forceinline__ void stream_out(const uint4 *S, uint32_t *out, int part, int parts, uint64_t out_words,
+                                           uint64_t alloc_words, int lt, int tg)
+{
+    constexpr int C3 = (int)pow3(kChunkDigits);
+    constexpr int NP = (int)(((uint64_t)R * C3 + 31) / 32);
+    const uint32_t *Sw = reinterpret_cast<const uint32_t *>(S);
+    auto packed = [&](int j) -> uint32_t {   // packed word j is at word 256 (j / 243) + j % 243
+        if (j < 0 || j >= NP) return 0u;
+        const int g = j / C3;
+        return Sw[256 * g + (j - g * C3)];
+    };
+    const uint64_t bit0 = (uint64_t)part * R * C3;
+    const int o = (int)(bit0 & 31);
+    const uint64_t W0 = bit0 >> 5;
+    constexpr uint64_t L = (uint64_t)R * C3;
+    const int nw = (int)((o + L + 31) >> 5);
+    const bool last = part == parts - 1;
+    const int tail = (int)((o + L) & 31);
+    for (int i = lt; i < nw; i += tg) {
+        const uint32_t val = o ? __funnelshift_l(packed(i - 1), packed(i), o) : packed(i);
+        const bool shared_prev = (i == 0 && o != 0);
+        const bool shared_next = (i == nw - 1 && !last && tail != 0);
+        uint32_t *dst = out + W0 + i;
+        if (!shared_prev && !shared_next) {
+            *dst = val;
+        } else {
+            uint32_t m = 0xffffffffu;
+            if (shared_prev) m &= 0xffffffffu << o;
+            if (shared_next) m &= (1u << tail) - 1u;
+            atomicAnd(dst, val | ~m);
+            atomicOr(dst, val & m);
+        }
+    }
+    if (last)
+        for (uint64_t w = out_words + lt; w < alloc_words; w += tg) out[w] = 0u;
+}
+
+__device__ __forceinline__ void add_count(unsigned long long *count, unsigned long long bits)
+{
+    for (int off = 16; off > 0; off >>= 1) bits += __shfl_down_sync(0xffffffffu, bits, off);
+    if ((threadIdx.x & 31) == 0 && bits) atomicAdd(count, bits);
+}
+
 template <int H, int CL, int D>
 __global__ void __launch_bounds__(1024, 1) fn_kernel(const FnArgs a)
 {
@@ -264,7 +401,6 @@ __global__ void __launch_bounds__(1024, 1) fn_kernel(const FnArgs a)
     constexpr int CD = (CL == 9) ? 2 : (CL == 3) ? 1 : 0;   // cluster digits
     constexpr int HL = H - CD;                              // high digits one CTA holds
     constexpr int R = (int)pow3(HL);
-    constexpr int NB = 1 << HL;
     extern __shared__ uint4 fsmem[];
 
     const int tg = (int)a.tg;
@@ -282,28 +418,7 @@ __global__ void __launch_bounds__(1024, 1) fn_kernel(const FnArgs a)
     const uint32_t *dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(a.arena + dco);
     uint32_t *out = reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]);
 
-    // Load: the binary rows from the truth table (word g holds the 32 minterms
-    // of binary row g), chunk digits merged on the way.
-    // Cluster digit c of this CTA is digit c of rank; word gb + 2^HL b0 +
-    // 2^(HL+1) b1 holds binary row gb with cluster digits (b0, b1); a '*'
-    // cluster digit ANDs both values.
-    const int cd0 = CD >= 1 ? rank % 3 : 0, cd1 = CD >= 2 ? rank / 3 : 0;
-    for (int gb = lt; gb < NB; gb += tg) {
-        uint32_t x = 0xffffffffu;
-#pragma unroll
-        for (int b1 = 0; b1 < (CD >= 2 ? 2 : 1); ++b1) {
-            if (CD >= 2 && cd1 != 2 && b1 != cd1) continue;
-#pragma unroll
-            for (int b0 = 0; b0 < (CD >= 1 ? 2 : 1); ++b0) {
-                if (CD >= 1 && cd0 != 2 && b0 != cd0) continue;
-                const int wi = gb + (b0 << HL) + (b1 << (HL + 1));
-                x &= __ldg(on + wi) | (dc ? __ldg(dc + wi) : 0u);
-            }
-        }
-        uint32_t v[kChunkWords];
-        chunk_merge_from_tt(x, v);
-        st_row(S, spread3k<HL>(gb), v);
-    }
+    load_rows<HL, CD>(S, on, dc, rank, lt, tg);
     sync();
     merge_all<HL, 0, D>(S, lt, tg, sync);
 
@@ -344,100 +459,76 @@ __global__ void __launch_bounds__(1024, 1) fn_kernel(const FnArgs a)
     }
     reduce_all<HL, 0, D>(S, lt, tg, sync);
 
-    // Chunk digits, count, and the rows packed into the dense stream in
-    // place: a warp takes regions of 32 rows (1 KB of shared memory; 32 rows
-    // of 243 cells are exactly 243 words), reduces each row's chunk digits in
-    // registers and writes the region's packed words to its start.  Lane l's
-    // row starts at bit 243 l of the region; the word it shares with the next
-    // row is completed by the next lane.
-    constexpr int C3 = (int)pow3(kChunkDigits);
-    constexpr int NREG = (R + 31) / 32;
-    constexpr int NP = (int)(((uint64_t)R * C3 + 31) / 32);   // packed words of this CTA
-    const int lane = (int)threadIdx.x & 31, nwarp = tg >> 5;
-    uint32_t *Sw = reinterpret_cast<uint32_t *>(S);
-    unsigned long long bits = 0;
-    {
-        const int sh = (C3 * lane) & 31, w0 = (C3 * lane) >> 5;
-        const bool k8 = sh + C3 > 256;                     // the row's last word is word 8 (else 7)
-        const bool shares = ((sh + C3) & 31) != 0;         // the next row starts inside it
-        for (int g = lt >> 5; g < NREG; g += nwarp) {
-            const int r = 32 * g + lane;
-            uint32_t v[kChunkWords];
-            if (r < R) {
-                ld_row(S, r, v);
-                chunk_reduce_row(v);
-            } else {
-#pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) v[w] = 0;
-            }
-#pragma unroll
-            for (int w = 0; w < kChunkWords; ++w) bits += __popc(v[w]);
-            uint32_t o[kChunkWords + 1];
-            o[0] = __funnelshift_l(0u, v[0], sh);
-#pragma unroll
-            for (int k = 1; k < kChunkWords; ++k) o[k] = __funnelshift_l(v[k - 1], v[k], sh);
-            o[kChunkWords] = __funnelshift_l(v[kChunkWords - 1], 0u, sh);
-            const uint32_t tailw = k8 ? o[8] : o[7];
-            const uint32_t from_prev = __shfl_up_sync(0xffffffffu, tailw, 1);
-            if (lane > 0 && sh != 0) o[0] |= from_prev;
-            __syncwarp();   // every row of the region is in registers before it is overwritten
-            if (r < R) {
-                const bool own_last = !shares || lane == 31 || r + 1 >= R;
-                uint32_t *dst = Sw + 256 * g + w0;
-#pragma unroll
-                for (int k = 0; k < 7; ++k) dst[k] = o[k];
-                if (k8 || own_last) dst[7] = o[7];
-                if (k8 && own_last) dst[8] = o[8];
-            }
-            __syncwarp();
-        }
-    }
-    for (int off = 16; off > 0; off >>= 1) bits += __shfl_down_sync(0xffffffffu, bits, off);
-    if (lane == 0 && bits) atomicAdd(a.count + id, bits);
-    sync();
-
-    // Packed word j of this CTA's stream is at word 256 (j / 243) + j % 243.
-    auto packed = [&](int j) -> uint32_t {
-        if (j < 0 || j >= NP) return 0u;
-        const int g = j / C3;
-        return Sw[256 * g + (j - g * C3)];
-    };
     if constexpr (CL == 1) {
-        // The whole bitmap slot in 16-byte stores (zeros past the stream).
-        const int n4 = (int)(a.out_alloc_words / 4);
-        uint4 *out4 = reinterpret_cast<uint4 *>(out);
-        for (int q = lt; q < n4; q += tg) {
-            const int j = 4 * q;
-            out4[q] = make_uint4(packed(j), packed(j + 1), packed(j + 2), packed(j + 3));
-        }
+        // a single CTA's stream starts at bit 0 of the bitmap: each region
+        // goes out as soon as it is packed (coalesced 4-byte stores)
+        add_count(a.count + id, chunk_pack<R, true>(S, out, lt, tg));
+        constexpr uint64_t NP = ((uint64_t)R * pow3(kChunkDigits) + 31) / 32;
+        for (uint64_t w = NP + lt; w < a.out_alloc_words; w += tg) out[w] = 0u;   // at most three words
     } else {
-        // CTA `rank` holds rows rank*R .. rank*R + R-1 of the function: its
-        // stream starts at bit rank*R*243.  Words shared with the neighbouring
-        // CTA of the cluster are written with masked atomics.
-        const uint64_t bit0 = (uint64_t)rank * R * C3;
-        const int o = (int)(bit0 & 31);
-        const uint64_t W0 = bit0 >> 5;
-        constexpr uint64_t L = (uint64_t)R * C3;
-        const int nw = (int)((o + L + 31) >> 5);
-        const bool last = rank == CL - 1;
-        const int tail = (int)((o + L) & 31);
-        for (int i = lt; i < nw; i += tg) {
-            const uint32_t val = o ? __funnelshift_l(packed(i - 1), packed(i), o) : packed(i);
-            const bool shared_prev = (i == 0 && o != 0);
-            const bool shared_next = (i == nw - 1 && !last && tail != 0);
-            uint32_t *dst = out + W0 + i;
-            if (!shared_prev && !shared_next) {
-                *dst = val;
-            } else {
-                uint32_t m = 0xffffffffu;
-                if (shared_prev) m &= 0xffffffffu << o;
-                if (shared_next) m &= (1u << tail) - 1u;
-                atomicAnd(dst, val | ~m);
-                atomicOr(dst, val & m);
+        add_count(a.count + id, chunk_pack<R, false>(S, out, lt, tg));
+        sync();
+        stream_out<R>(S, out, rank, CL, a.out_words, a.out_alloc_words, lt, tg);
+    }
+}
+
+// n = 14 in one CTA: the three thirds of the top high digit one after the
+// other (persistent: CTA b takes functions b, b + grid, ...).  The '*' third
+// is merged first and parked in a scratch slot of the CTA's own in device
+// memory (210 KB, read back from L2); thirds 0 and 1 are merged, cleared by
+// it (Reduce of the top digit), reduced and written out; then the '*' third
+// comes back, is reduced and written out.
+template <int D>
+__global__ void __launch_bounds__(1024, 1) fn_thirds_kernel(const FnArgs a)
+{
+    constexpr int HL = 8, R = (int)pow3(HL);
+    extern __shared__ uint4 fsmem[];
+    const int tg = (int)blockDim.x, lt = (int)threadIdx.x;
+    const SubSync sync{1, tg, true};
+    uint4 *S = fsmem;
+    uint4 *T = a.scratch + (size_t)blockIdx.x * 2 * R;
+    for (uint64_t fi = blockIdx.x; fi < a.nfun; fi += gridDim.x) {
+        const uint32_t id = a.fn[fi];
+        const uint32_t *on = reinterpret_cast<const uint32_t *>(a.arena + a.tt_off[id]);
+        const uint64_t dco = a.dc_off[id];
+        const uint32_t *dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(a.arena + dco);
+        uint32_t *out = reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]);
+        unsigned long long bits = 0;
+
+        load_rows<HL, 1>(S, on, dc, 2, lt, tg);
+        sync();
+        merge_all<HL, 0, D>(S, lt, tg, sync);
+        for (int i = lt; i < 2 * R; i += tg) T[i] = S[i];
+        sync();   // the scratch copy is complete (and visible to the block) before S is reused
+        for (int part = 0; part < 2; ++part) {
+            load_rows<HL, 1>(S, on, dc, part, lt, tg);
+            sync();
+            merge_all<HL, 0, D>(S, lt, tg, sync);
+            for (int i = lt; i < 2 * R; i += tg) {
+                const uint4 z = T[i];
+                uint4 v = S[i];
+                v.x &= ~z.x; v.y &= ~z.y; v.z &= ~z.z; v.w &= ~z.w;
+                S[i] = v;
             }
+            sync();
+            reduce_all<HL, 0, D>(S, lt, tg, sync);
+            if (part == 0) {
+                bits += chunk_pack<R, true>(S, out, lt, tg);   // third 0 starts at bit 0
+            } else {
+                bits += chunk_pack<R, false>(S, out, lt, tg);
+                sync();
+                stream_out<R>(S, out, part, 3, a.out_words, a.out_alloc_words, lt, tg);
+            }
+            sync();
         }
-        if (last)
-            for (uint64_t w = a.out_words + lt; w < a.out_alloc_words; w += tg) out[w] = 0u;
+        for (int i = lt; i < 2 * R; i += tg) S[i] = T[i];
+        sync();
+        reduce_all<HL, 0, D>(S, lt, tg, sync);
+        bits += chunk_pack<R, false>(S, out, lt, tg);
+        sync();
+        stream_out<R>(S, out, 2, 3, a.out_words, a.out_alloc_words, lt, tg);
+        add_count(a.count + id, bits);
+        sync();   // S and T are free for the next function
     }
 }
 
@@ -489,10 +580,21 @@ static cudaError_t launch_fn_d(int n, int cl, const FnArgs &a, uint32_t ctas, si
     return cudaErrorInvalidValue;
 }
 
+template <int D>
+static cudaError_t launch_thirds(const FnArgs &a, uint32_t ctas, size_t smem, cudaStream_t s)
+{
+    auto kern = fn_thirds_kernel<D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ctas, a.tg, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 uint64_t fn_smem_bytes(int n, int fpc, int ctas)
 {
     if (n < kFnMinN || n > kFnMaxN) return 0;
-    const int cd = ctas == 9 ? 2 : ctas == 3 ? 1 : 0;
+    // one CTA for n = 14 holds one third at a time
+    const int cd = ctas == 9 ? 2 : (ctas == 3 || n == 14) ? 1 : 0;
     return (uint64_t)fpc * pow3(n - kChunkDigits - cd) * kChunkBytes;
 }
 
@@ -502,7 +604,8 @@ bool fn_config_ok(int n, const FnConfig &c)
     if (c.digits != 2 && c.digits != 3) return false;
     if (c.tg < 32 || c.tg % 32 || c.fpc < 1 || c.fpc > 15) return false;
     if (c.tg * c.fpc > 1024) return false;
-    // clusters: 3 CTAs for n = 13 and 14, 9 for n = 14, one function each
+    // clusters: 3 CTAs for n = 13 and 14, 9 for n = 14, one function each;
+    // one CTA for n = 14 runs the thirds in turn
     if (c.ctas == 3 && n != 13 && n != 14) return false;
     if (c.ctas == 9 && n != 14) return false;
     if (c.ctas != 1 && c.ctas != 3 && c.ctas != 9) return false;
@@ -527,8 +630,15 @@ cudaError_t launch_fn_batch(int n, const BatchArgs &b, const FnConfig &c, cudaSt
     a.count = b.count;
     a.out_words = bitmap_words(n);
     a.out_alloc_words = bitmap_alloc_bytes(n) / 4;
-    const uint32_t groups = (b.nfun + c.fpc - 1) / c.fpc;   // CTAs, or clusters
     const size_t smem = fn_smem_bytes(n, c.fpc, c.ctas);
+    if (n == 14 && c.ctas == 1) {
+        // persistent: at most one CTA per scratch slot
+        if (!b.scratch || b.scratch_ctas == 0) return cudaErrorInvalidValue;
+        a.scratch = static_cast<uint4 *>(b.scratch);
+        const uint32_t ctas = b.nfun < b.scratch_ctas ? b.nfun : b.scratch_ctas;
+        return c.digits >= 3 ? launch_thirds<3>(a, ctas, smem, s) : launch_thirds<2>(a, ctas, smem, s);
+    }
+    const uint32_t groups = (b.nfun + c.fpc - 1) / c.fpc;   // CTAs, or clusters
     return c.digits >= 3 ? launch_fn_d<3>(n, c.ctas, a, groups, smem, s)
                          : launch_fn_d<2>(n, c.ctas, a, groups, smem, s);
 }

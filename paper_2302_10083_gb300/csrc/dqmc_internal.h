@@ -130,6 +130,8 @@ struct BatchArgs {
     const uint8_t *arena = nullptr;
     uint8_t *bitmaps = nullptr;
     unsigned long long *count = nullptr;   // one per function id
+    void *scratch = nullptr;               // n = 14 in one CTA: 3^8 * 32 bytes per CTA slot
+    uint32_t scratch_ctas = 0;
 };
 
 // Enqueue the whole sweep.  d_count must point to a uint64 (zeroed here).
@@ -176,10 +178,13 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 // Whole functions in shared memory (dqmc_fn.cu), 5 <= n <= 14: tg threads
 // per function, fpc functions per CTA, the high digits merged and reduced
 // `digits` (2 or 3) at a time; or one function per cluster of ctas = 3
-// (n = 13, 14) or 9 (n = 14) CTAs.
+// (n = 13, 14) or 9 (n = 14) CTAs; or, for n = 14 with ctas = 1, one CTA per
+// function doing the three thirds of the top digit in turn (persistent, with
+// BatchArgs::scratch).
 constexpr int kFnMinN = 5;
 constexpr int kFnMaxN = 14;
 constexpr uint64_t kFnMaxSmem = 232448;    // 227 KB of shared memory per CTA
+constexpr uint64_t kFnThirdBytes = 6561ull * 32;   // one third of an n = 14 state (3^8 rows)
 struct FnConfig {
     int tg = 256;
     int fpc = 1;

@@ -106,7 +106,10 @@ def test_batch_workspace_and_layout():
             cfg = dict(path=dqmc.DQMC_BATCH_PATH_SMEM, threads_per_fn=256, fns_per_cta=1, digits_per_step=2,
                        ctas_per_fn=3 if n == 14 else 1)
             assert dqmc.dqmc_batch_set_config(n, cfg) == 0
-        assert dqmc.dqmc_batch_workspace_bytes(np.array([13, 14, 14])) < 1 << 16
+        # no states; n = 14 keeps a scratch third (3^8 rows) per CTA slot of its one-CTA kernel
+        assert dqmc.dqmc_batch_workspace_bytes(np.array([13])) < 1 << 16
+        w14 = dqmc.dqmc_batch_workspace_bytes(np.array([13, 14, 14]))
+        assert w14 % (3 ** 8 * 32) < 1 << 16 and 64 * 3 ** 8 * 32 <= w14 < 1024 * 3 ** 8 * 32
     finally:
         dqmc.load_batch_tuning(saved)
     assert dqmc.dqmc_batch_workspace_bytes(np.array([15])) == 0
@@ -428,7 +431,8 @@ def test_batch_config_rules_without_gpu():
             assert c["path"] in (S, T) and (c["path"] == T or 5 <= n <= 14)
             assert dqmc.dqmc_batch_set_config(n, _cfg(T, 0, 0, 0, 0)) == dqmc.DQMC_OK
         ok = [(5, 32, 15, 2), (5, 32, 8, 3), (12, 512, 1, 3), (12, 64, 3, 2), (13, 1024, 1, 2), (12, 1024, 1, 3),
-              (14, 512, 1, 3, 3), (14, 32, 1, 2, 9), (14, 1024, 1, 3, 9), (13, 256, 1, 2, 3), (10, 96, 3, 3)]
+              (14, 512, 1, 3, 3), (14, 32, 1, 2, 9), (14, 1024, 1, 3, 9), (13, 256, 1, 2, 3), (10, 96, 3, 3),
+              (14, 1024, 1, 3, 1)]     # one CTA doing the thirds of the top digit in turn
         bad = [(4, 32, 1, 2),        # below the chunk size
                (15, 32, 1, 2),       # above the batch range
                (8, 48, 1, 2),        # not whole warps
@@ -437,8 +441,8 @@ def test_batch_config_rules_without_gpu():
                (8, 512, 4, 2),       # 2048 threads
                (12, 64, 4, 2),       # 4 x 70 KB of shared memory
                (13, 64, 2, 2),       # 2 x 210 KB
-               (14, 64, 1, 2),       # 630 KB in one CTA
                (14, 64, 2, 2, 3),    # clusters hold one function
+               (14, 64, 2, 2, 1),    # 2 x 210 KB
                (13, 64, 1, 2, 9),    # nine CTAs only for n = 14
                (12, 64, 1, 2, 3),    # clusters only for n = 13, 14
                (14, 64, 1, 2, 2),    # 1, 3 or 9 CTAs

@@ -147,14 +147,15 @@ def test_batch_each_path_bit_exact(path, table):
 
 # (n, threads per function, functions per CTA, digits per step, CTAs per
 # function): every n of the shared-memory path, both step sizes, one warp up
-# to 1024 threads, clusters of 3 and 9, and CTAs whose last functions are
-# missing (13 functions per batch).
+# to 1024 threads, clusters of 3 and 9, one CTA doing the thirds of n = 14 in
+# turn, and CTAs whose last functions are missing (13 functions per batch).
 SMEM_SHAPES = [
     (5, 32, 8, 2, 1), (5, 64, 3, 3, 1), (6, 32, 6, 3, 1), (7, 32, 4, 2, 1), (8, 64, 4, 3, 1), (8, 32, 15, 2, 1),
     (9, 128, 2, 2, 1), (9, 32, 1, 3, 1), (10, 96, 3, 3, 1), (10, 1024, 1, 2, 1), (11, 256, 2, 2, 1),
     (11, 32, 1, 3, 1), (12, 512, 1, 3, 1), (12, 128, 3, 2, 1), (12, 1024, 1, 3, 1), (13, 512, 1, 3, 1),
     (13, 1024, 1, 2, 1), (13, 64, 1, 2, 1), (13, 256, 1, 3, 3), (13, 1024, 1, 2, 3), (14, 512, 1, 3, 3),
     (14, 1024, 1, 2, 3), (14, 128, 1, 3, 3), (14, 256, 1, 3, 9), (14, 1024, 1, 2, 9), (14, 64, 1, 3, 9),
+    (14, 1024, 1, 3, 1), (14, 256, 1, 2, 1),
 ]
 
 
