@@ -299,3 +299,14 @@ def test_n24_workload_sampled():
     """n = 24, ON ~ Bernoulli(0.85), seed 1 (the benchmark workload)."""
     on, _ = synth.single_n24(1)
     sampled_check(24, on, None, 0.85)
+
+
+def test_n25_stretch_sampled():
+    """n = 25, ON ~ Bernoulli(0.85), seed 1: the largest size (state 111.6 GB +
+    bitmap 105.9 GB in device memory), sampled as at n = 24."""
+    free, _ = torch.cuda.mem_get_info()
+    need = dqmc.dqmc_workspace_bytes(25) + dqmc.dqmc_bitmap_alloc_bytes(25) + int(1.1e9) * 8
+    if free < need:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+    on, _ = synth.random_function(25, 1, 0.85)
+    sampled_check(25, on, None, 0.85, n_list=5000, n_cells=50000)
