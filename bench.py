@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--serve-jobs", type=int, default=2000, help="serving: jobs per arrival rate at most")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving: arrival span per rate at most")
     ap.add_argument("--batch", type=int, default=65536, help="functions in the batched workload")
+    ap.add_argument("--batch-n", type=int, default=None,
+                    help="batched: every function with this n (a one-class batch, for profiling one kernel)")
     ap.add_argument("--no-one-by-one", action="store_true",
                     help="batched: skip the one-launch-per-function comparison (for profiling the graph alone)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -137,13 +139,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sel)}
 
 
+# The sources the streaming pass kernels are compiled from: a change to any of
+# them voids the stored ncu traffic of those kernels.
+PASS_SOURCES = ("dqmc_chunk.cuh", "dqmc_internal.h", "dqmc_pass.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_10083_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in PASS_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -303,13 +309,14 @@ def run_ours(args, rank, world, local):
     A = (cubes + 7) // 8
     b_roof = (1 << n) // 8 + 3 * A
     result = {
-        "metric": "cubes/s (dense prime-implicant sweep, n=24 single function)",
+        "metric": f"cubes/s (dense prime-implicant sweep, n={n} single function)",
         "value": value, "unit": "cubes/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 bitwise", "data": "synthetic",
         "config": {"workload": f"single function n={n}, ON ~ Bernoulli({P_ON}), seed 1+rank, no don't-cares; "
                                f"step = full sweep + bitmap + count + (mask,value) list, inputs resident in HBM",
-                   "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state 37 GB and bitmap 35 GB >> 129 MB L2",
+                   "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state %.0f GB and bitmap %.0f GB >> 129 MB L2" % (
+                       dqmc.dqmc_workspace_bytes(n) / 1e9, A / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -382,7 +389,10 @@ def run_batched(args, rank, world, local):
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
-    b = synth.batch_functions(count=args.batch, seed=1 + rank)
+    if args.batch_n is None:
+        b = synth.batch_functions(count=args.batch, seed=1 + rank)
+    else:
+        b = synth.batch_functions(count=args.batch, seed=1 + rank, n_lo=args.batch_n, n_hi=args.batch_n)
     ns = b["n"].astype(np.uint32)
     nf = len(ns)
     arena_h = torch.from_numpy(b["arena"]).pin_memory()
@@ -486,7 +496,8 @@ def report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, s
     cubes = int(sum(3 ** int(n) for n in ns))
     value = world * nf / (ms / 1e3)
     result = {
-        "metric": f"functions/s (batched: {nf} functions, n uniform in 4..14)", "value": value,
+        "metric": f"functions/s (batched: {nf} functions, " + (
+            "n uniform in 4..14)" if args.batch_n is None else f"all n = {args.batch_n})"), "value": value,
         "unit": "functions/s", "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bitwise",
         "data": "synthetic",
