@@ -686,8 +686,75 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
         // neighbours lie above it), so once a round's reads of a row are
         // done, that row of the round's units is free: the reduce passes put
         // the reduced row back in place, the bitmap pass stages dense bits there.
+        if constexpr (MODE == kModeOut) {
+            static_assert(kRounds == 2, "the bitmap pass holds two units per thread");
+            // Both of a thread's units (u0 = tid, u1 = tid + NT) reduce row k
+            // before one barrier, then both write it back: row k of a unit is
+            // read only while rows k are reduced (and its row 2 by the unit
+            // itself before that), so one barrier per row covers the tile.
+            const int u0 = tid, u1 = tid + NT;
+            const bool v1 = u1 < kUnits;
+            int se0[6 - D0], so0[6 - D0], se1[6 - D0], so1[6 - D0];
+            auto slots = [&](int u, bool valid, int (&se)[6 - D0], int (&so)[6 - D0]) {
+                const uint32_t code = valid ? (uint32_t)S.code[u] : 0u;
+                static_for<D0, 6>([&](auto Dg) {
+                    constexpr int d = decltype(Dg)::value;
+                    constexpr int Dd = (int)pow3(d);
+                    const uint32_t lit = (code >> d) & 1u, one = (code >> (8 + d)) & 1u;
+                    const int nb = u + (int)(2u - one) * Dd;
+                    se[d - D0] = lit ? uslot(nb, 0) : kZeroSlot;
+                    so[d - D0] = lit ? uslot(nb, 1) : kZeroSlot + 1;
+                });
+            };
+            slots(u0, true, se0, so0);
+            slots(u1, v1, se1, so1);
+            auto finish = [&](int u, const int (&se)[6 - D0], const int (&so)[6 - D0], int k,
+                              uint32_t (&xr)[kChunkWords]) {
+                uint32_t acc[kChunkWords];
+                if (k < 2) {
+                    // tile digit 0: rows 0 and 1 lose what row 2 ('*') holds
+                    const uint4 q0 = tile[uslot(u, 4)], q1 = tile[uslot(u, 5)];
+                    acc[0] = q0.x; acc[1] = q0.y; acc[2] = q0.z; acc[3] = q0.w;
+                    acc[4] = q1.x; acc[5] = q1.y; acc[6] = q1.z; acc[7] = q1.w;
+                } else {
+#pragma unroll
+                    for (int w = 0; w < kChunkWords; ++w) acc[w] = 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < 6 - D0; ++i) {
+                    const uint4 a0 = tile[se[i] + 2 * k], a1 = tile[so[i] + 2 * k];
+                    acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
+                    acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
+                }
+                const uint4 q0 = tile[uslot(u, 2 * k)], q1 = tile[uslot(u, 2 * k + 1)];
+                xr[0] = q0.x; xr[1] = q0.y; xr[2] = q0.z; xr[3] = q0.w;
+                xr[4] = q1.x; xr[5] = q1.y; xr[6] = q1.z; xr[7] = q1.w;
+                chunk_reduce_p<CM>(xr, acc);
+#pragma unroll
+                for (int w = 0; w < kChunkWords; ++w) xr[w] &= ~acc[w];
+            };
 #pragma unroll 1
-        for (int rd = 0; rd < kRounds; ++rd) {
+            for (int k = 0; k < 3; ++k) {
+                uint32_t x0[kChunkWords], x1[kChunkWords];
+                finish(u0, se0, so0, k, x0);
+#pragma unroll
+                for (int w = 0; w < kChunkWords; ++w) my_count += __popc(x0[w]);
+                if (v1) {
+                    finish(u1, se1, so1, k, x1);
+#pragma unroll
+                    for (int w = 0; w < kChunkWords; ++w) my_count += __popc(x1[w]);
+                }
+                __syncthreads();
+                tile[uslot(u0, 2 * k)] = make_uint4(x0[0], x0[1], x0[2], x0[3]);
+                tile[uslot(u0, 2 * k + 1)] = make_uint4(x0[4], x0[5], x0[6], x0[7]);
+                if (v1) {
+                    tile[uslot(u1, 2 * k)] = make_uint4(x1[0], x1[1], x1[2], x1[3]);
+                    tile[uslot(u1, 2 * k + 1)] = make_uint4(x1[4], x1[5], x1[6], x1[7]);
+                }
+            }
+        }
+#pragma unroll 1
+        for (int rd = 0; rd < (MODE == kModeOut ? 0 : kRounds); ++rd) {
             const int u = rd * NT + tid;
             const bool valid = u < kUnits;
             // Slots of the '*' neighbour of u in each group digit d: digit
