@@ -35,6 +35,7 @@
 
 #include "dqmc_chunk.cuh"
 #include "dqmc_internal.h"
+#include "dqmc_steps.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -75,30 +76,6 @@ __device__ __forceinline__ void st_row(uint4 *S, int r, const uint32_t (&v)[kChu
 {
     S[fslot(r, 0)] = make_uint4(v[0], v[1], v[2], v[3]);
     S[fslot(r, 1)] = make_uint4(v[4], v[5], v[6], v[7]);
-}
-
-// sum of 3^i over the set bits i of x (x < 2^K)
-template <int K>
-__device__ __forceinline__ int spread3k(int x)
-{
-    int r = 0;
-#pragma unroll
-    for (int i = 0; i < K; ++i) r += ((x >> i) & 1) * (int)pow3(i);
-    return r;
-}
-
-// Compile-time digit helpers over block indices t < 3^D.
-__host__ __device__ constexpr int twos_of(int t, int D)
-{
-    int c = 0;
-    for (int i = 0; i < D; ++i, t /= 3) c += (t % 3) == 2;
-    return c;
-}
-__host__ __device__ constexpr bool binary_above(int t, int d, int D)
-{
-    for (int i = 0; i < D; ++i, t /= 3)
-        if (i > d && (t % 3) == 2) return false;
-    return true;
 }
 
 // The 32 minterms of a chunk -> its 243 cells, Merged over the five chunk
@@ -142,121 +119,6 @@ __device__ __forceinline__ void chunk_reduce_row(uint32_t (&v)[kChunkWords])
     });
 #pragma unroll
     for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
-}
-
-struct SubSync {
-    int id, nthreads;
-    bool whole;
-    __device__ __forceinline__ void operator()() const
-    {
-        if (whole) __syncthreads();
-        else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
-    }
-};
-
-// Merge of digits J .. J+DD-1 (of the HL digits a CTA holds): blocks of
-// 3^DD rows whose lower digits take any value and whose higher digits are 0/1.
-template <int HL, int J, int DD>
-__device__ __forceinline__ void merge_step(uint4 *S, int lt, int tg)
-{
-    constexpr int P = (int)pow3(J);
-    constexpr int T = (int)pow3(DD);
-    constexpr int items = P * (1 << (HL - J - DD)) * 4;
-    for (int it = lt; it < items; it += tg) {
-        const int q = it & 3, r = it >> 2;
-        const int lo = r % P, hb = r / P;
-        const int base = lo + (int)pow3(J + DD) * spread3k<HL - J - DD>(hb);
-        uint2 *bp = reinterpret_cast<uint2 *>(S) + 4 * base + q;   // slice q of row base
-        uint2 x[T];
-        static_for<0, T>([&](auto Ti) {
-            constexpr int t = decltype(Ti)::value;
-            if constexpr (twos_of(t, DD) == 0) x[t] = bp[4 * t * P];
-        });
-        static_for<0, DD>([&](auto Di) {
-            constexpr int d = decltype(Di)::value;
-            constexpr int w = (int)pow3(d);
-            static_for<0, T>([&](auto Ti) {
-                constexpr int t = decltype(Ti)::value;
-                if constexpr ((t / w) % 3 == 2 && binary_above(t, d, DD)) {
-                    x[t].x = x[t - 2 * w].x & x[t - w].x;
-                    x[t].y = x[t - 2 * w].y & x[t - w].y;
-                }
-            });
-        });
-        static_for<0, T>([&](auto Ti) {
-            constexpr int t = decltype(Ti)::value;
-            if constexpr (twos_of(t, DD) > 0) bp[4 * t * P] = x[t];
-        });
-    }
-}
-
-// Reduce of digits J .. J+DD-1 over all rows: each cell loses its bit if one
-// of its '*' neighbours in these digits is set, all read from the block as
-// the step found it (rows are updated in order of their number of '*'
-// digits, so a row is overwritten only after every row that reads it).
-template <int HL, int J, int DD>
-__device__ __forceinline__ void reduce_step(uint4 *S, int lt, int tg)
-{
-    constexpr int P = (int)pow3(J);
-    constexpr int T = (int)pow3(DD);
-    constexpr int items = (int)pow3(HL - DD) * 4;
-    for (int it = lt; it < items; it += tg) {
-        const int q = it & 3, r = it >> 2;
-        const int lo = r % P, hi = r / P;
-        const int base = lo + hi * (int)pow3(J + DD);
-        uint2 *bp = reinterpret_cast<uint2 *>(S) + 4 * base + q;   // slice q of row base
-        uint2 x[T];
-        static_for<0, T>([&](auto Ti) {
-            constexpr int t = decltype(Ti)::value;
-            x[t] = bp[4 * t * P];
-        });
-        static_for<0, DD>([&](auto Ki) {
-            constexpr int k = decltype(Ki)::value;   // number of '*' digits of the rows updated now
-            static_for<0, T>([&](auto Ti) {
-                constexpr int t = decltype(Ti)::value;
-                if constexpr (twos_of(t, DD) == k) {
-                    uint32_t ax = 0, ay = 0;
-                    static_for<0, DD>([&](auto Di) {
-                        constexpr int d = decltype(Di)::value;
-                        constexpr int w = (int)pow3(d);
-                        constexpr int td = (t / w) % 3;
-                        if constexpr (td != 2) {
-                            ax |= x[t + (2 - td) * w].x;
-                            ay |= x[t + (2 - td) * w].y;
-                        }
-                    });
-                    x[t].x &= ~ax;
-                    x[t].y &= ~ay;
-                }
-            });
-        });
-        static_for<0, T>([&](auto Ti) {
-            constexpr int t = decltype(Ti)::value;
-            if constexpr (twos_of(t, DD) < DD) bp[4 * t * P] = x[t];
-        });
-    }
-}
-
-template <int HL, int J, int D>
-__device__ __forceinline__ void merge_all(uint4 *S, int lt, int tg, const SubSync &sync)
-{
-    if constexpr (J < HL) {
-        constexpr int DD = (HL - J < D) ? HL - J : D;
-        merge_step<HL, J, DD>(S, lt, tg);
-        sync();
-        merge_all<HL, J + DD, D>(S, lt, tg, sync);
-    }
-}
-
-template <int HL, int J, int D>
-__device__ __forceinline__ void reduce_all(uint4 *S, int lt, int tg, const SubSync &sync)
-{
-    if constexpr (J < HL) {
-        constexpr int DD = (HL - J < D) ? HL - J : D;
-        reduce_step<HL, J, DD>(S, lt, tg);
-        sync();
-        reduce_all<HL, J + DD, D>(S, lt, tg, sync);
-    }
 }
 
 // Binary rows of one part of a function from its truth table (word g holds

@@ -43,6 +43,7 @@
 
 #include "dqmc_chunk.cuh"
 #include "dqmc_internal.h"
+#include "dqmc_steps.cuh"
 
 namespace dqmc {
 
@@ -1102,6 +1103,85 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 
 // ------------------------------------------------------------------ dispatch
 
+// ------------------------------------------------------ last Merge pass
+// The last Merge pass on whole rows: a tile's 3^7 rows (inner digits 0..B-1,
+// then group digits B..6 = high digits a..a+K-1) in shared memory, row-major
+// with no swizzle (dqmc_steps.cuh).  The rows whose group digits are 0/1 come
+// in; the group digits are merged and then reduced kMrDigits at a time, one
+// barrier per step; each row's chunk digits are reduced in registers; the
+// rows go out from their threads when a group digit's rows are less than
+// 1 MB apart, else back in place and out with consecutive lanes on
+// consecutive 16-byte pieces (STAGE).
+constexpr int kMrThreads = 384;
+constexpr int kMrDigits = 3;
+
+template <int K, int B, int CM, bool STAGE>
+__global__ void __launch_bounds__(kMrThreads, 3) mr_pass_kernel(const __grid_constant__ PassParams P)
+{
+    constexpr int NT = kMrThreads;
+    constexpr int R = kTileRows;
+    constexpr int RE = (int)pow3(B);   // inner rows per group-digit value
+    constexpr int NB = 1 << K;
+    static_assert(K + B == kTileDigits && B >= 1, "tiles are 3^7 rows with at least one inner digit");
+    extern __shared__ uint4 tile[];
+    __shared__ PassShared S;
+    const int tid = threadIdx.x;
+    const FnBufs F = fn_bufs(P);
+    if (tid == 0) decode_tile0<false>(P, S, F.tile);
+    __syncthreads();
+    const uint64_t base = S.base, w_g = P.w_g, state_rows = P.state_rows;
+    uint4 *const state = F.state;
+    // tile row e + RE*g (e: inner digits, g: group digits) is state row base + e + g*w_g
+    auto state_row = [&](int ri) -> uint64_t {
+        const int g = ri / RE, e = ri - g * RE;
+        return base + (uint64_t)e + (uint64_t)g * w_g;
+    };
+
+    // load the rows whose group digits are all 0/1
+    for (int p = tid; p < NB * RE * 2; p += NT) {
+        const int h = p & 1, q = p >> 1;
+        const int gb = q / RE, e = q - gb * RE;
+        const int g = (int)__ldg(&g_tab.sp3[gb]);
+        const uint64_t row = base + (uint64_t)e + (uint64_t)g * w_g;
+        if (!ck(P, row < state_rows, row)) continue;
+        cp_async16p(&tile[2 * (e + RE * g) + h], &state[2 * row + h]);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const SubSync sync{1, NT, true};
+    __syncthreads();
+
+    merge_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
+    reduce_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
+
+    // chunk digits, then out
+    for (int ri = tid; ri < R; ri += NT) {
+        const uint4 q0 = tile[2 * ri], q1 = tile[2 * ri + 1];
+        uint32_t v[kChunkWords] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        uint32_t acc[kChunkWords] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        chunk_reduce_p<CM>(v, acc);
+#pragma unroll
+        for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
+        if constexpr (STAGE) {
+            // only this thread reads or writes row ri in this loop
+            tile[2 * ri] = make_uint4(v[0], v[1], v[2], v[3]);
+            tile[2 * ri + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+        } else {
+            const uint64_t row = state_row(ri);
+            if (!ck(P, row < state_rows, row)) continue;
+            state[2 * row] = make_uint4(v[0], v[1], v[2], v[3]);
+            state[2 * row + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+        }
+    }
+    if constexpr (STAGE) {
+        __syncthreads();
+        for (int p = tid; p < 2 * R; p += NT) {
+            const uint64_t row = state_row(p >> 1);
+            if (!ck(P, row < state_rows, row)) continue;
+            state[2 * row + (p & 1)] = tile[p];
+        }
+    }
+}
+
 template <typename Kern>
 static cudaError_t launch_tiles(Kern kern, size_t smem, const PassParams &p, uint64_t tiles, cudaStream_t stream,
                                int threads = kThreads)
@@ -1130,6 +1210,30 @@ static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t
             return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream,
                                 unit_threads<MODE>());
     return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, false>, smem, p, tiles, stream, unit_threads<MODE>());
+}
+
+template <int K, int CM>
+static cudaError_t launch_mr(const PassParams &p, uint64_t tiles, cudaStream_t stream)
+{
+    constexpr int B = kTileDigits - K;
+    const size_t smem = (size_t)kTileRows * kChunkBytes;
+    if (p.w_g * kChunkBytes >= kStageStrideBytes)
+        return launch_tiles(mr_pass_kernel<K, B, CM, true>, smem, p, tiles, stream, kMrThreads);
+    return launch_tiles(mr_pass_kernel<K, B, CM, false>, smem, p, tiles, stream, kMrThreads);
+}
+
+template <int CM>
+static cudaError_t dispatch_mr(int K, const PassParams &p, uint64_t tiles, cudaStream_t s)
+{
+    switch (K) {
+    case 1: return launch_mr<1, CM>(p, tiles, s);
+    case 2: return launch_mr<2, CM>(p, tiles, s);
+    case 3: return launch_mr<3, CM>(p, tiles, s);
+    case 4: return launch_mr<4, CM>(p, tiles, s);
+    case 5: return launch_mr<5, CM>(p, tiles, s);
+    case 6: return launch_mr<6, CM>(p, tiles, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int LOAD, int MODE, int CM>
@@ -1210,9 +1314,9 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
         else if (ph.out)
             e = cudaErrorInvalidValue;
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x03)
-            e = dispatch_group<kLoadSparse, kModeMergeReduce, 0x03>(ph.K, a, tiles, stream);
+            e = dispatch_mr<0x03>(ph.K, a, tiles, stream);
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x07)
-            e = dispatch_group<kLoadSparse, kModeMergeReduce, 0x07>(ph.K, a, tiles, stream);
+            e = dispatch_mr<0x07>(ph.K, a, tiles, stream);
         else if (ph.merge && !ph.reduce && ph.chunk_mask == 0)
             e = dispatch_group<kLoadSparse, kModeMerge, 0>(ph.K, a, tiles, stream);
         else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x1c)
