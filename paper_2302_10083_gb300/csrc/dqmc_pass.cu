@@ -1103,19 +1103,20 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 
 // ------------------------------------------------------------------ dispatch
 
-// ------------------------------------------------------ last Merge pass
-// The last Merge pass on whole rows: a tile's 3^7 rows (inner digits 0..B-1,
-// then group digits B..6 = high digits a..a+K-1) in shared memory, row-major
-// with no swizzle (dqmc_steps.cuh).  The rows whose group digits are 0/1 come
-// in; the group digits are merged and then reduced kMrDigits at a time, one
-// barrier per step; each row's chunk digits are reduced in registers; the
-// rows go out from their threads when a group digit's rows are less than
-// 1 MB apart, else back in place and out with consecutive lanes on
-// consecutive 16-byte pieces (STAGE).
+// --------------------------------------- last Merge pass and Reduce passes
+// Whole rows: a tile's 3^7 rows (inner digits 0..B-1, then group digits B..6
+// = high digits a..a+K-1) in shared memory, row-major with no swizzle
+// (dqmc_steps.cuh).  MERGE (the last Merge pass): the rows whose group digits
+// are 0/1 come in and the group digits are merged kMrDigits at a time; else
+// every row comes in.  Then the group digits are reduced kMrDigits at a time
+// (one barrier per step), each row's chunk digits in registers, and the rows
+// go out from their threads when a group digit's rows are less than 1 MB
+// apart, else back in place and out with consecutive lanes on consecutive
+// 16-byte pieces (STAGE).
 constexpr int kMrThreads = 384;
 constexpr int kMrDigits = 3;
 
-template <int K, int B, int CM, bool STAGE>
+template <int K, int B, int CM, bool STAGE, bool MERGE>
 __global__ void __launch_bounds__(kMrThreads, 3) mr_pass_kernel(const __grid_constant__ PassParams P)
 {
     constexpr int NT = kMrThreads;
@@ -1137,20 +1138,28 @@ __global__ void __launch_bounds__(kMrThreads, 3) mr_pass_kernel(const __grid_con
         return base + (uint64_t)e + (uint64_t)g * w_g;
     };
 
-    // load the rows whose group digits are all 0/1
-    for (int p = tid; p < NB * RE * 2; p += NT) {
-        const int h = p & 1, q = p >> 1;
-        const int gb = q / RE, e = q - gb * RE;
-        const int g = (int)__ldg(&g_tab.sp3[gb]);
-        const uint64_t row = base + (uint64_t)e + (uint64_t)g * w_g;
-        if (!ck(P, row < state_rows, row)) continue;
-        cp_async16p(&tile[2 * (e + RE * g) + h], &state[2 * row + h]);
+    if constexpr (MERGE) {
+        // the rows whose group digits are all 0/1
+        for (int p = tid; p < NB * RE * 2; p += NT) {
+            const int h = p & 1, q = p >> 1;
+            const int gb = q / RE, e = q - gb * RE;
+            const int g = (int)__ldg(&g_tab.sp3[gb]);
+            const uint64_t row = base + (uint64_t)e + (uint64_t)g * w_g;
+            if (!ck(P, row < state_rows, row)) continue;
+            cp_async16p(&tile[2 * (e + RE * g) + h], &state[2 * row + h]);
+        }
+    } else {
+        for (int p = tid; p < 2 * R; p += NT) {
+            const uint64_t row = state_row(p >> 1);
+            if (!ck(P, row < state_rows, row)) continue;
+            cp_async16p(&tile[p], &state[2 * row + (p & 1)]);
+        }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     const SubSync sync{1, NT, true};
     __syncthreads();
 
-    merge_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
+    if constexpr (MERGE) merge_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
     reduce_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
 
     // chunk digits, then out
@@ -1212,26 +1221,26 @@ static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t
     return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, false>, smem, p, tiles, stream, unit_threads<MODE>());
 }
 
-template <int K, int CM>
+template <int K, int CM, bool MERGE>
 static cudaError_t launch_mr(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
     constexpr int B = kTileDigits - K;
     const size_t smem = (size_t)kTileRows * kChunkBytes;
     if (p.w_g * kChunkBytes >= kStageStrideBytes)
-        return launch_tiles(mr_pass_kernel<K, B, CM, true>, smem, p, tiles, stream, kMrThreads);
-    return launch_tiles(mr_pass_kernel<K, B, CM, false>, smem, p, tiles, stream, kMrThreads);
+        return launch_tiles(mr_pass_kernel<K, B, CM, true, MERGE>, smem, p, tiles, stream, kMrThreads);
+    return launch_tiles(mr_pass_kernel<K, B, CM, false, MERGE>, smem, p, tiles, stream, kMrThreads);
 }
 
-template <int CM>
+template <int CM, bool MERGE>
 static cudaError_t dispatch_mr(int K, const PassParams &p, uint64_t tiles, cudaStream_t s)
 {
     switch (K) {
-    case 1: return launch_mr<1, CM>(p, tiles, s);
-    case 2: return launch_mr<2, CM>(p, tiles, s);
-    case 3: return launch_mr<3, CM>(p, tiles, s);
-    case 4: return launch_mr<4, CM>(p, tiles, s);
-    case 5: return launch_mr<5, CM>(p, tiles, s);
-    case 6: return launch_mr<6, CM>(p, tiles, s);
+    case 1: return launch_mr<1, CM, MERGE>(p, tiles, s);
+    case 2: return launch_mr<2, CM, MERGE>(p, tiles, s);
+    case 3: return launch_mr<3, CM, MERGE>(p, tiles, s);
+    case 4: return launch_mr<4, CM, MERGE>(p, tiles, s);
+    case 5: return launch_mr<5, CM, MERGE>(p, tiles, s);
+    case 6: return launch_mr<6, CM, MERGE>(p, tiles, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1314,15 +1323,15 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
         else if (ph.out)
             e = cudaErrorInvalidValue;
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x03)
-            e = dispatch_mr<0x03>(ph.K, a, tiles, stream);
+            e = dispatch_mr<0x03, true>(ph.K, a, tiles, stream);
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x07)
-            e = dispatch_mr<0x07>(ph.K, a, tiles, stream);
+            e = dispatch_mr<0x07, true>(ph.K, a, tiles, stream);
         else if (ph.merge && !ph.reduce && ph.chunk_mask == 0)
             e = dispatch_group<kLoadSparse, kModeMerge, 0>(ph.K, a, tiles, stream);
         else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x1c)
-            e = dispatch_group<kLoadFull, kModeReduce, 0x1c>(ph.K, a, tiles, stream);
+            e = dispatch_mr<0x1c, false>(ph.K, a, tiles, stream);
         else if (!ph.merge && ph.reduce && ph.chunk_mask == 0)
-            e = dispatch_group<kLoadFull, kModeReduce, 0>(ph.K, a, tiles, stream);
+            e = dispatch_mr<0, false>(ph.K, a, tiles, stream);
         else
             e = cudaErrorInvalidValue;  // not a pass the plan makes
         if (e != cudaSuccess) return e;
