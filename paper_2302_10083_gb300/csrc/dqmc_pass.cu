@@ -50,12 +50,11 @@ namespace dqmc {
 static __constant__ MaskTable kMasksP = make_mask_table();
 
 constexpr int kUnits = kTileRows / 3;  // 729 units of three rows per tile
-// Shared memory of a unit pass, in 16-byte slots: the tile (6 slots per unit,
-// plus, in the padded layout, one free slot after every four units; see
-// uslot), then one unit of zeros that stands for the '*' neighbour a '*'
+// Shared memory of a unit pass, in 16-byte slots: the tile (6 slots per unit;
+// see uslot), then one unit of zeros that stands for the '*' neighbour a '*'
 // digit does not have.
 template <bool PAD>
-constexpr int tile_slots() { return 6 * kUnits + (PAD ? (kUnits + 3) / 4 : 0); }
+constexpr int tile_slots() { return 6 * kUnits; }
 template <bool PAD>
 constexpr size_t unit_smem() { return (size_t)(tile_slots<PAD>() + 6) * 16; }
 
@@ -159,7 +158,8 @@ __device__ __forceinline__ FnBufs fn_bufs(const PassParams &P)
     return f;
 }
 
-constexpr int kThreads = 256;       // threads per CTA of the first pass and the Reduce passes (80 registers)
+constexpr int kThreads = 256;       // threads per CTA of the first pass
+constexpr int kOutStepDigits = 3;   // bitmap pass: tile digits reduced per step
 constexpr int kOutThreads = 384;    // threads per CTA of the bitmap pass and the Merge-only passes
 constexpr int kMaxWarps = kOutThreads / 32;
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
@@ -169,8 +169,8 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 // (800 words); their 32 * 729 bits, starting at bit o < 32, take at most 730
 // words.  The last region has 729 - 22 * 32 = 25 units (6 * 25 + 6 slots).
 static_assert(kUnits == 22 * 32 + 25, "tile units");
-static_assert((31 + 32 * 729 + 31) / 32 <= 4 * (6 * 32 + 8), "full staging fits its region");
-static_assert((31 + 25 * 729 + 31) / 32 <= 4 * (6 * 25 + 6), "tail staging fits its region");
+static_assert((31 + 32 * 729 + 31) / 32 <= 4 * (6 * 32), "full staging fits its region");
+static_assert((31 + 25 * 729 + 31) / 32 <= 4 * (6 * 25), "tail staging fits its region");
 
 enum PassMode : int { kModeMerge = 0, kModeMergeReduce = 1, kModeReduce = 2, kModeOut = 3 };
 
@@ -188,18 +188,18 @@ __device__ __forceinline__ bool ck(const PassParams &P, bool cond, uint64_t idx)
     return false;
 }
 
-// Shared-memory slot (uint4) of 16-byte piece c (row c/2, half c%2) of unit u.
-// Both layouts keep the eight lanes of a quarter-warp on eight different
-// 16-byte bank groups when they read the same piece of consecutive units:
-//   padded (PAD): the unit's 96 bytes are contiguous, as in the state (so a
-//     bulk copy moves four units at once), with one free slot after every four
-//     units (6u + u/4 mod 8 = 0 6 4 2 1 7 5 3);
-//   swizzled: every other group of four units has its row halves swapped,
-//     which also keeps units three apart (the Merge of unit digit 0) apart.
+// Shared-memory slot (uint4) of 16-byte piece c (row c/2, half c%2) of unit u:
+//   plain (PAD, the bitmap pass): row-major as in the state, row r at bytes
+//     32r .. 32r+31, so bulk copies move whole runs of units and the Merge /
+//     Reduce steps of dqmc_steps.cuh work on it;
+//   swizzled (the Merge-only passes): every other group of four units has its
+//     row halves swapped, so that the eight lanes of a quarter-warp reading the
+//     same piece of consecutive units (or of units three apart, the Merge of
+//     unit digit 0) hit eight different 16-byte bank groups.
 template <bool PAD>
 __device__ __forceinline__ int uslot(int u, int c)
 {
-    if constexpr (PAD) return 6 * u + (u >> 2) + c;
+    if constexpr (PAD) return 6 * u + c;
     else return 6 * u + (c ^ ((u >> 2) & 1));
 }
 
@@ -688,70 +688,25 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
         // done, that row of the round's units is free: the reduce passes put
         // the reduced row back in place, the bitmap pass stages dense bits there.
         if constexpr (MODE == kModeOut) {
-            static_assert(kRounds == 2, "the bitmap pass holds two units per thread");
-            // Both of a thread's units (u0 = tid, u1 = tid + NT) reduce row k
-            // before one barrier, then both write it back: row k of a unit is
-            // read only while rows k are reduced (and its row 2 by the unit
-            // itself before that), so one barrier per row covers the tile.
-            const int u0 = tid, u1 = tid + NT;
-            const bool v1 = u1 < kUnits;
-            int se0[6 - D0], so0[6 - D0], se1[6 - D0], so1[6 - D0];
-            auto slots = [&](int u, bool valid, int (&se)[6 - D0], int (&so)[6 - D0]) {
-                const uint32_t code = valid ? (uint32_t)S.code[u] : 0u;
-                static_for<D0, 6>([&](auto Dg) {
-                    constexpr int d = decltype(Dg)::value;
-                    constexpr int Dd = (int)pow3(d);
-                    const uint32_t lit = (code >> d) & 1u, one = (code >> (8 + d)) & 1u;
-                    const int nb = u + (int)(2u - one) * Dd;
-                    se[d - D0] = lit ? uslot(nb, 0) : kZeroSlot;
-                    so[d - D0] = lit ? uslot(nb, 1) : kZeroSlot + 1;
-                });
-            };
-            slots(u0, true, se0, so0);
-            slots(u1, v1, se1, so1);
-            auto finish = [&](int u, const int (&se)[6 - D0], const int (&so)[6 - D0], int k,
-                              uint32_t (&xr)[kChunkWords]) {
-                uint32_t acc[kChunkWords];
-                if (k < 2) {
-                    // tile digit 0: rows 0 and 1 lose what row 2 ('*') holds
-                    const uint4 q0 = tile[uslot(u, 4)], q1 = tile[uslot(u, 5)];
-                    acc[0] = q0.x; acc[1] = q0.y; acc[2] = q0.z; acc[3] = q0.w;
-                    acc[4] = q1.x; acc[5] = q1.y; acc[6] = q1.z; acc[7] = q1.w;
-                } else {
+            // Reduce of tile digits 0..6 on whole rows (the tile is row-major),
+            // three digits per step with one barrier each (dqmc_steps.cuh); then
+            // each thread reduces the chunk digits of its rows (if this pass has
+            // any) and counts them.
+            const SubSync sync{1, NT, true};
+            reduce_all<kTileDigits, 0, kOutStepDigits>(tile, tid, NT, sync);
+            for (int r = tid; r < kTileRows; r += NT) {
+                const uint4 q0 = tile[2 * r], q1 = tile[2 * r + 1];
+                uint32_t v[kChunkWords] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                if constexpr (CM != 0) {
+                    uint32_t acc[kChunkWords] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                    chunk_reduce_p<CM>(v, acc);
 #pragma unroll
-                    for (int w = 0; w < kChunkWords; ++w) acc[w] = 0u;
+                    for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
+                    tile[2 * r] = make_uint4(v[0], v[1], v[2], v[3]);     // only this thread touches row r here
+                    tile[2 * r + 1] = make_uint4(v[4], v[5], v[6], v[7]);
                 }
 #pragma unroll
-                for (int i = 0; i < 6 - D0; ++i) {
-                    const uint4 a0 = tile[se[i] + 2 * k], a1 = tile[so[i] + 2 * k];
-                    acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
-                    acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
-                }
-                const uint4 q0 = tile[uslot(u, 2 * k)], q1 = tile[uslot(u, 2 * k + 1)];
-                xr[0] = q0.x; xr[1] = q0.y; xr[2] = q0.z; xr[3] = q0.w;
-                xr[4] = q1.x; xr[5] = q1.y; xr[6] = q1.z; xr[7] = q1.w;
-                chunk_reduce_p<CM>(xr, acc);
-#pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) xr[w] &= ~acc[w];
-            };
-#pragma unroll 1
-            for (int k = 0; k < 3; ++k) {
-                uint32_t x0[kChunkWords], x1[kChunkWords];
-                finish(u0, se0, so0, k, x0);
-#pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) my_count += __popc(x0[w]);
-                if (v1) {
-                    finish(u1, se1, so1, k, x1);
-#pragma unroll
-                    for (int w = 0; w < kChunkWords; ++w) my_count += __popc(x1[w]);
-                }
-                __syncthreads();
-                tile[uslot(u0, 2 * k)] = make_uint4(x0[0], x0[1], x0[2], x0[3]);
-                tile[uslot(u0, 2 * k + 1)] = make_uint4(x0[4], x0[5], x0[6], x0[7]);
-                if (v1) {
-                    tile[uslot(u1, 2 * k)] = make_uint4(x1[0], x1[1], x1[2], x1[3]);
-                    tile[uslot(u1, 2 * k + 1)] = make_uint4(x1[4], x1[5], x1[6], x1[7]);
-                }
+                for (int w = 0; w < kChunkWords; ++w) my_count += __popc(v[w]);
             }
         }
 #pragma unroll 1
