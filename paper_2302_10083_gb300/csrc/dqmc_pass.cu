@@ -1067,14 +1067,17 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 // (one barrier per step), each row's chunk digits in registers, and the rows
 // go out from their threads when a group digit's rows are less than 1 MB
 // apart, else back in place and out with consecutive lanes on consecutive
-// 16-byte pieces (STAGE).
-constexpr int kMrThreads = 384;
-constexpr int kMrDigits = 3;
+// 16-byte pieces (STAGE).  kMrDigits per step, mr_threads per CTA.
+// Threads per CTA and digits per step (measured at n = 24: the last Merge
+// pass 14.70 ms with 384 threads and 2 digits, 14.81 with 384 and 3; the
+// middle Reduce pass 14.78 ms with 256 and 2, 17.26 with 384 and 3).
+template <bool MERGE> constexpr int mr_threads() { return MERGE ? 384 : 256; }
+constexpr int kMrDigits = 2;
 
 template <int K, int B, int CM, bool STAGE, bool MERGE>
-__global__ void __launch_bounds__(kMrThreads, 3) mr_pass_kernel(const __grid_constant__ PassParams P)
+__global__ void __launch_bounds__(mr_threads<MERGE>(), 3) mr_pass_kernel(const __grid_constant__ PassParams P)
 {
-    constexpr int NT = kMrThreads;
+    constexpr int NT = mr_threads<MERGE>();
     constexpr int R = kTileRows;
     constexpr int RE = (int)pow3(B);   // inner rows per group-digit value
     constexpr int NB = 1 << K;
@@ -1182,8 +1185,8 @@ static cudaError_t launch_mr(const PassParams &p, uint64_t tiles, cudaStream_t s
     constexpr int B = kTileDigits - K;
     const size_t smem = (size_t)kTileRows * kChunkBytes;
     if (p.w_g * kChunkBytes >= kStageStrideBytes)
-        return launch_tiles(mr_pass_kernel<K, B, CM, true, MERGE>, smem, p, tiles, stream, kMrThreads);
-    return launch_tiles(mr_pass_kernel<K, B, CM, false, MERGE>, smem, p, tiles, stream, kMrThreads);
+        return launch_tiles(mr_pass_kernel<K, B, CM, true, MERGE>, smem, p, tiles, stream, mr_threads<MERGE>());
+    return launch_tiles(mr_pass_kernel<K, B, CM, false, MERGE>, smem, p, tiles, stream, mr_threads<MERGE>());
 }
 
 template <int CM, bool MERGE>
