@@ -172,7 +172,9 @@ static_assert(kUnits == 22 * 32 + 25, "tile units");
 static_assert((31 + 32 * 729 + 31) / 32 <= 4 * (6 * 32), "full staging fits its region");
 static_assert((31 + 25 * 729 + 31) / 32 <= 4 * (6 * 25), "tail staging fits its region");
 
-enum PassMode : int { kModeMerge = 0, kModeMergeReduce = 1, kModeReduce = 2, kModeOut = 3 };
+// Modes of unit_pass_kernel (the last Merge pass and the Reduce passes run in
+// mr_pass_kernel).
+enum PassMode : int { kModeMerge = 0, kModeOut = 3 };
 
 __device__ __forceinline__ void report(const PassParams &P, uint64_t idx)
 {
@@ -532,11 +534,11 @@ __device__ __noinline__ void emit_from_bitmap(const PassParams &P, PassShared &S
 template <int MODE>
 constexpr int unit_threads() { return (MODE == kModeOut || MODE == kModeMerge) ? kOutThreads : kThreads; }
 
-template <int K, int B, int LOAD, int MODE, int CM, bool STAGE>
+template <int K, int B, int LOAD, int MODE, int CM>
 __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(const __grid_constant__ PassParams P)
 {
     constexpr int NT = unit_threads<MODE>();
-    constexpr int kRounds = (kUnits + NT - 1) / NT;   // rounds of units per tile
+    static_assert(MODE == kModeMerge || MODE == kModeOut, "Merge-only and bitmap passes (the others: mr_pass_kernel)");
     static_assert(K + B == kTileDigits, "tiles are 3^7 rows");
     static_assert(B >= 1 || (MODE == kModeOut && LOAD == kLoadFull), "B = 0 only in the bitmap pass");
     constexpr int RU = (B == 0) ? 1 : (int)pow3(B - 1);
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
     }
 
     // --------------------------------------------------------------- Merge
-    if constexpr (MODE == kModeMerge || MODE == kModeMergeReduce) {
+    if constexpr (MODE == kModeMerge) {
         static_for<0, K>([&](auto J) {
             constexpr int d = D0 + decltype(J)::value;
             constexpr int Dd = (int)pow3(d);
@@ -683,11 +685,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
         const uint64_t W0 = bit0 >> 5;
         const bool last_tile = (base + kTileRows == P.total_rows);
 
-        // A unit is read only by units of smaller or equal index (its '*'
-        // neighbours lie above it), so once a round's reads of a row are
-        // done, that row of the round's units is free: the reduce passes put
-        // the reduced row back in place, the bitmap pass stages dense bits there.
-        if constexpr (MODE == kModeOut) {
+        {
             // Reduce of tile digits 0..6 on whole rows (the tile is row-major),
             // three digits per step with one barrier each (dqmc_steps.cuh); then
             // each thread reduces the chunk digits of its rows (if this pass has
@@ -709,90 +707,6 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                 for (int w = 0; w < kChunkWords; ++w) my_count += __popc(v[w]);
             }
         }
-#pragma unroll 1
-        for (int rd = 0; rd < (MODE == kModeOut ? 0 : kRounds); ++rd) {
-            const int u = rd * NT + tid;
-            const bool valid = u < kUnits;
-            // Slots of the '*' neighbour of u in each group digit d: digit
-            // 0 -> u + 2*3^d, 1 -> u + 3^d, '*' -> the zero unit; se: even
-            // pieces (first row halves), so: odd pieces.
-            int se[6 - D0], so[6 - D0];
-            {
-                const uint32_t code = valid ? (uint32_t)S.code[u] : 0u;
-                static_for<D0, 6>([&](auto Dg) {
-                    constexpr int d = decltype(Dg)::value;
-                    constexpr int Dd = (int)pow3(d);
-                    const uint32_t lit = (code >> d) & 1u, one = (code >> (8 + d)) & 1u;
-                    const int nb = u + (int)(2u - one) * Dd;
-                    se[d - D0] = lit ? uslot(nb, 0) : kZeroSlot;
-                    so[d - D0] = lit ? uslot(nb, 1) : kZeroSlot + 1;
-                });
-            }
-            // row k of the unit: OR of its '*' neighbours, chunk digits,
-            // then the row loses those cells
-            auto finish_row = [&](int k, uint32_t (&xr)[kChunkWords]) {
-                uint32_t acc[kChunkWords];
-                if (B == 0 && k < 2) {
-                    // tile digit 0: rows 0 and 1 lose what row 2 ('*') holds
-                    const uint4 q0 = tile[uslot(u, 4)], q1 = tile[uslot(u, 5)];
-                    acc[0] = q0.x; acc[1] = q0.y; acc[2] = q0.z; acc[3] = q0.w;
-                    acc[4] = q1.x; acc[5] = q1.y; acc[6] = q1.z; acc[7] = q1.w;
-                } else {
-#pragma unroll
-                    for (int w = 0; w < kChunkWords; ++w) acc[w] = 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < 6 - D0; ++i) {
-                    const uint4 a0 = tile[se[i] + 2 * k], a1 = tile[so[i] + 2 * k];
-                    acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
-                    acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
-                }
-                const uint4 q0 = tile[uslot(u, 2 * k)], q1 = tile[uslot(u, 2 * k + 1)];
-                xr[0] = q0.x; xr[1] = q0.y; xr[2] = q0.z; xr[3] = q0.w;
-                xr[4] = q1.x; xr[5] = q1.y; xr[6] = q1.z; xr[7] = q1.w;
-                chunk_reduce_p<CM>(xr, acc);
-#pragma unroll
-                for (int w = 0; w < kChunkWords; ++w) xr[w] &= ~acc[w];
-            };
-
-            if constexpr (STAGE || MODE == kModeOut) {
-                // Row k of a unit is read only while rows k are reduced (and,
-                // in the bitmap pass, row 2 by its own unit before that): the
-                // reduced row goes back to its slot after this round's reads.
-#pragma unroll 1
-                for (int k = 0; k < 3; ++k) {
-                    uint32_t xr[kChunkWords];
-                    if (valid) {
-                        finish_row(k, xr);
-                        if constexpr (MODE == kModeOut) {
-#pragma unroll
-                            for (int w = 0; w < kChunkWords; ++w) my_count += __popc(xr[w]);
-                        }
-                    }
-                    __syncthreads();
-                    if (valid) {
-                        tile[uslot(u, 2 * k)] = make_uint4(xr[0], xr[1], xr[2], xr[3]);
-                        tile[uslot(u, 2 * k + 1)] = make_uint4(xr[4], xr[5], xr[6], xr[7]);
-                    }
-                }
-            } else if constexpr (MODE != kModeOut) {
-                // reduced rows straight to the state
-                if (valid) {
-                    const uint64_t row0 = unit_row(u);
-                    const bool row_ok = ck(P, row0 + 2 < state_rows, row0 + 2);
-#pragma unroll 1
-                    for (int k = 0; k < 3; ++k) {
-                        uint32_t xr[kChunkWords];
-                        finish_row(k, xr);
-                        if (row_ok) {
-                            state[2 * (row0 + k)] = make_uint4(xr[0], xr[1], xr[2], xr[3]);
-                            state[2 * (row0 + k) + 1] = make_uint4(xr[4], xr[5], xr[6], xr[7]);
-                        }
-                    }
-                }
-            }
-        }
-
         if constexpr (MODE == kModeOut) {
             // ------------------------------------------------ bitmap and list
             // The tile now holds the reduced rows, and the rounds counted
@@ -983,17 +897,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
             }
         }
 
-        if constexpr (MODE != kModeOut && STAGE) {
-            // reduced tile -> state, consecutive lanes on consecutive 16-byte
-            // pieces of a unit's three rows
-            __syncthreads();
-            for (int p = tid; p < kUnits * 6; p += NT) {
-                const int uu = p / 6, c = p - 6 * uu;
-                const uint64_t row0 = unit_row(uu);
-                if (!ck(P, row0 + 2 < state_rows, row0 + 2)) continue;
-                state[2 * row0 + c] = tile[uslot(uu, c)];
-            }
-        } else if constexpr (MODE == kModeOut) {
+        if constexpr (MODE == kModeOut) {
             if (last_tile)
                 for (uint64_t w = P.out_words + tid; w < P.out_alloc_words; w += NT) out[w] = 0u;
             if (P.pairs) {
@@ -1161,22 +1065,17 @@ static cudaError_t launch_tiles(Kern kern, size_t smem, const PassParams &p, uin
     return cudaGetLastError();
 }
 
-// Units of a group digit lie 3^a rows apart in the state.  When that is
-// 1 MB or more, the threads of a warp would each store to another page, so
-// the reduce passes put their rows back in shared memory and store the tile
-// with consecutive lanes on consecutive pieces (STAGE) instead of storing
-// each unit's rows from its thread.
+// A group digit's rows lie 3^a rows apart in the state.  When that is 1 MB or
+// more, a warp storing one row per thread would touch many pages, so the row
+// passes put their rows back in shared memory and store the tile with
+// consecutive lanes on consecutive 16-byte pieces (STAGE) instead.
 constexpr uint64_t kStageStrideBytes = 1ull << 20;
 
 template <int K, int B, int LOAD, int MODE, int CM>
 static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
-    size_t smem = unit_smem<B == 0>();
-    if constexpr (MODE == kModeMergeReduce || MODE == kModeReduce)
-        if (p.w_g * kChunkBytes >= kStageStrideBytes)
-            return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, true>, smem, p, tiles, stream,
-                                unit_threads<MODE>());
-    return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM, false>, smem, p, tiles, stream, unit_threads<MODE>());
+    return launch_tiles(unit_pass_kernel<K, B, LOAD, MODE, CM>, unit_smem<B == 0>(), p, tiles, stream,
+                        unit_threads<MODE>());
 }
 
 template <int K, int CM, bool MERGE>
