@@ -100,7 +100,11 @@ int dqmc_count(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
 /* The primes as (mask, value) pairs in ascending rho (the output extraction
  * step of Algorithm 4, Section 4.2).  out_pairs: caller-owned, 2*cap uint32.
  * *out_count receives the number of primes even when it exceeds cap
- * (status DQMC_ETRUNC, first cap pairs written). */
+ * (status DQMC_ETRUNC, first cap pairs written).  When out_pairs is pinned
+ * host memory the device can address (cudaHostAlloc / cudaHostRegister,
+ * 8-byte aligned), the kernels write the list into it directly (over
+ * NVLink-C2C on a Grace-based node) and no copy follows the sweep; otherwise
+ * the list goes through a device buffer and one copy. */
 int dqmc_list(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
               uint32_t *out_pairs, uint64_t cap, uint64_t *out_count);
 

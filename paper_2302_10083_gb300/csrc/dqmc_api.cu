@@ -536,15 +536,31 @@ static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, 
     if (dc_bits && (st = ensure(c, 1, tt_alloc))) return st;
     if ((st = ensure(c, 2, bitmap_alloc_bytes((int)n)))) return st;
     if ((st = ensure(c, 3, w.total))) return st;
-    if (want_list && cap && (st = ensure(c, 4, 8 * cap))) return st;
+    // A list buffer in pinned host memory that the device can address (8-byte
+    // aligned) is written by the kernels directly (over NVLink-C2C on a
+    // Grace-based node), so the list needs no copy after the sweep; any other
+    // buffer gets the list through a device buffer and one copy.
+    uint32_t *d_pairs = nullptr;
+    bool direct = false;
+    if (want_list && cap) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, out_pairs) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer && (uintptr_t)pa.devicePointer % 8 == 0) {
+            d_pairs = static_cast<uint32_t *>(pa.devicePointer);
+            direct = true;
+        } else {
+            cudaGetLastError();   // pageable memory: not an error
+            if ((st = ensure(c, 4, 8 * cap))) return st;
+            d_pairs = static_cast<uint32_t *>(c->buf[4]);
+        }
+    }
     cudaStream_t s = c->stream;
     cudaError_t e = cudaMemcpyAsync(c->buf[0], on_bits, tt, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && dc_bits) e = cudaMemcpyAsync(c->buf[1], dc_bits, tt, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return map_cuda(e);
     uint64_t *dcount = reinterpret_cast<uint64_t *>(c->d_count);
     if (want_list)
-        st = dqmc_list_dev(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, c->buf[2],
-                           static_cast<uint32_t *>(cap ? c->buf[4] : nullptr), cap, dcount, c->buf[3],
+        st = dqmc_list_dev(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, c->buf[2], d_pairs, cap, dcount, c->buf[3],
                            c->cap[3], s);
     else
         st = dqmc_primes_dev(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, c->buf[2], dcount, c->buf[3],
@@ -558,7 +574,7 @@ static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, 
     if ((st = dqmc_dev_status(n, c->buf[3], c->cap[3], s))) return st;
     const uint64_t count = *c->h_count;
     if (out_count) *out_count = count;
-    if (want_list && cap) {
+    if (want_list && cap && !direct) {
         const uint64_t k = count < cap ? count : cap;
         if (k) {
             e = cudaMemcpy(out_pairs, c->buf[4], 8 * k, cudaMemcpyDeviceToHost);

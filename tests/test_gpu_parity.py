@@ -310,3 +310,24 @@ def test_n25_stretch_sampled():
         pytest.skip(f"needs {need / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
     on, _ = synth.random_function(25, 1, 0.85)
     sampled_check(25, on, None, 0.85, n_list=5000, n_cells=50000)
+
+
+@pytest.mark.parametrize("n", [11, 17, 20])
+def test_list_into_pinned_host_memory(n):
+    """dqmc_list into pinned host memory (written by the kernels directly)
+    equals the list through pageable memory (device buffer and a copy), also
+    when truncated."""
+    import ctypes
+    on, dc = synth.random_function(n, 40 + n, 0.75, 0.05)
+    want, count = dqmc.dqmc_list(n, on, dc)
+    L = dqmc.lib()
+    for cap in (count, count // 3):
+        pinned = torch.full((2 * max(cap, 1) + 2,), -1, dtype=torch.int32).pin_memory()
+        c = ctypes.c_uint64()
+        st = L.dqmc_list(n, dqmc._p8(on), dqmc._p8(dc), ctypes.cast(pinned.data_ptr(), dqmc.c_u32p), cap,
+                         ctypes.byref(c))
+        assert st == (dqmc.DQMC_OK if cap >= count else dqmc.DQMC_ETRUNC)
+        assert int(c.value) == count
+        got = pinned.numpy().view(np.uint32)[: 2 * cap].reshape(cap, 2)
+        assert np.array_equal(got, want[:cap])
+        assert (pinned.numpy()[2 * cap:] == -1).all()   # nothing past cap
