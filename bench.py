@@ -315,7 +315,7 @@ def run_ours(args, rank, world, local):
         "dtype": "u32 bitwise", "data": "synthetic",
         "config": {"workload": f"single function n={n}, ON ~ Bernoulli({P_ON}), seed 1+rank, no don't-cares; "
                                f"step = full sweep + bitmap + count + (mask,value) list, inputs resident in HBM",
-                   "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state %.0f GB and bitmap %.0f GB >> 129 MB L2" % (
+                   "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state %.2f GB and bitmap %.2f GB >> 129 MB L2" % (
                        dqmc.dqmc_workspace_bytes(n) / 1e9, A / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
