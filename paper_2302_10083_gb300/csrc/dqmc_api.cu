@@ -30,10 +30,10 @@ uint64_t bitmap_alloc_bytes(int n) { return align_up((pow3(n) + 7) / 8, 16); }
 // plus 7 - K inner digits (the lowest high digits) for contiguous runs.
 //   first       truth table -> Merge chunk digits and G0 (digits >= 7 still 0/1)
 //   merge       Merge G1 .. G(last-1), sparse rows in and out
-//   merge-last  Merge the last group, then Reduce it and chunk digits {0, 1}
-//               (all of {0, 1, 2} when there is no middle group)
+//   merge-last  Merge the last group, then Reduce it (and chunk digits
+//               {0, 1, 2} when there is no middle group)
 //   reduce      Reduce the middle groups, top down; the first of them also
-//               Reduces chunk digits {2, 3, 4}
+//               Reduces all five chunk digits
 //   out         Reduce G0 (and chunk digits {3, 4} when there is no middle
 //               group), write the dense bitmap, the count and the list.
 // Every digit is merged once before any Reduce and reduced exactly once.
@@ -130,7 +130,10 @@ Plan make_plan(int n)
         sp.ph[0].merge = 1;
         if (i == ng - 1) {
             sp.ph[0].reduce = 1;
-            sp.ph[0].chunk_mask = (ng >= 2) ? 0x03 : 0x07;
+            // with a middle Reduce pass to come, that pass takes every chunk
+            // digit: it is bound by device memory with ALU to spare, while
+            // this pass is not (at n = 24, chunk digits {0, 1} cost it 3.8 ms)
+            sp.ph[0].chunk_mask = (ng >= 2) ? 0 : 0x07;
         }
         push(sp);
         for (int d = a; d < a + K; ++d) merged[d] = true;
@@ -139,7 +142,7 @@ Plan make_plan(int n)
         const int a = starts[i], K = sizes[i], B = kTileDigits - K;
         SuperPassDesc sp = make_pass(kLoadFull, a, K, B, H, merged);
         sp.ph[0].reduce = 1;
-        sp.ph[0].chunk_mask = (i == ng - 2) ? 0x1c : 0;
+        sp.ph[0].chunk_mask = (i == ng - 2) ? 0x1f : 0;
         push(sp);
     }
     {   // out: G0, the bitmap, the count and the list

@@ -1179,14 +1179,14 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
             e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0x18>(a, tiles, stream);
         else if (ph.out)
             e = cudaErrorInvalidValue;
-        else if (ph.merge && ph.reduce && ph.chunk_mask == 0x03)
-            e = dispatch_mr<0x03, true>(ph.K, a, tiles, stream);
+        else if (ph.merge && ph.reduce && ph.chunk_mask == 0)
+            e = dispatch_mr<0, true>(ph.K, a, tiles, stream);
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x07)
             e = dispatch_mr<0x07, true>(ph.K, a, tiles, stream);
         else if (ph.merge && !ph.reduce && ph.chunk_mask == 0)
             e = dispatch_group<kLoadSparse, kModeMerge, 0>(ph.K, a, tiles, stream);
-        else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x1c)
-            e = dispatch_mr<0x1c, false>(ph.K, a, tiles, stream);
+        else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x1f)
+            e = dispatch_mr<0x1f, false>(ph.K, a, tiles, stream);
         else if (!ph.merge && ph.reduce && ph.chunk_mask == 0)
             e = dispatch_mr<0, false>(ph.K, a, tiles, stream);
         else
