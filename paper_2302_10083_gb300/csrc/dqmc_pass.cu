@@ -556,9 +556,21 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
         decode_tile0<MODE == kModeOut>(P, S, F.tile);
         S.overflow = 0;
         if constexpr (B == 0) {
+            // The bitmap pass's tile is one contiguous block of the state (and
+            // of shared memory): thread 0 starts its copy (six TMA bulk copies)
+            // at once, before the first barrier.  A tile past the state is
+            // reported and not loaded; the bounded wait below then gives up.
             S.load_fail = 0;
             mbar_init(&S.bar, 1);
             mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
+            constexpr uint32_t kPart = (uint32_t)(kTileRows * kChunkBytes / 6);
+            static_assert(kTileRows * kChunkBytes % 6 == 0 && kPart % 16 == 0, "16-byte multiples");
+            const uint64_t last = S.base + kTileRows - 1;
+            if (ck(P, last < P.state_rows, last)) {
+                const char *src = reinterpret_cast<const char *>(&F.state[2 * S.base]);
+                for (int q = 0; q < 6; ++q)
+                    bulk_g2s(reinterpret_cast<char *>(tile) + q * kPart, src + q * kPart, kPart, &S.bar);
+            }
         }
     }
     __syncthreads();
@@ -584,18 +596,10 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
     };
 
     // ---------------------------------------------------------------- load
-    // The bitmap pass's tile is one contiguous block of the state: bulk
-    // copies (TMA) of four units (384 bytes) at a time, completing on one
+    // The bitmap pass's tile is in flight (issued above) and completes on one
     // mbarrier whose wait is bounded.  Other tiles are 96-byte runs far apart:
     // cp.async of 16-byte pieces, consecutive lanes on consecutive pieces.
     if constexpr (B == 0) {
-        for (int q = 4 * tid; q < kUnits; q += 4 * NT) {
-            const int nu = min(4, kUnits - q);
-            const uint64_t row0 = unit_row(q);
-            const uint64_t last = row0 + 3u * (uint64_t)nu - 1u;
-            if (!ck(P, last < state_rows, last)) continue;   // the wait below then gives up
-            bulk_g2s(&tile[uslot(q, 0)], &state[2 * row0], 96u * (uint32_t)nu, &S.bar);
-        }
         if (tid < 6) tile[kZeroSlot + tid] = make_uint4(0u, 0u, 0u, 0u);
         fill_tables();
         const uint64_t t0 = globaltimer_p();
