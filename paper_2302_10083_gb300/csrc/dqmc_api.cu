@@ -33,9 +33,9 @@ uint64_t bitmap_alloc_bytes(int n) { return align_up((pow3(n) + 7) / 8, 16); }
 //   merge-last  Merge the last group, then Reduce it (and chunk digits
 //               {0, 1, 2} when there is no middle group)
 //   reduce      Reduce the middle groups, top down; the first of them also
-//               Reduces all five chunk digits
-//   out         Reduce G0 (and chunk digits {3, 4} when there is no middle
-//               group), write the dense bitmap, the count and the list.
+//               Reduces chunk digits {0, 1, 2}
+//   out         Reduce G0 and chunk digits {3, 4}, write the dense bitmap,
+//               the count and the list.
 // Every digit is merged once before any Reduce and reduced exactly once.
 
 static FixedDigits fixed_of(const std::vector<int> &digits, const std::vector<bool> &merged)
@@ -130,9 +130,9 @@ Plan make_plan(int n)
         sp.ph[0].merge = 1;
         if (i == ng - 1) {
             sp.ph[0].reduce = 1;
-            // with a middle Reduce pass to come, that pass takes every chunk
-            // digit: it is bound by device memory with ALU to spare, while
-            // this pass is not (at n = 24, chunk digits {0, 1} cost it 3.8 ms)
+            // with a middle Reduce pass to come, that pass and the bitmap pass
+            // take the chunk digits instead (at n = 24, chunk digits {0, 1}
+            // cost this pass 3.8 ms and the middle Reduce 3.0 ms)
             sp.ph[0].chunk_mask = (ng >= 2) ? 0 : 0x07;
         }
         push(sp);
@@ -142,14 +142,14 @@ Plan make_plan(int n)
         const int a = starts[i], K = sizes[i], B = kTileDigits - K;
         SuperPassDesc sp = make_pass(kLoadFull, a, K, B, H, merged);
         sp.ph[0].reduce = 1;
-        sp.ph[0].chunk_mask = (i == ng - 2) ? 0x1f : 0;
+        sp.ph[0].chunk_mask = (i == ng - 2) ? 0x07 : 0;
         push(sp);
     }
     {   // out: G0, the bitmap, the count and the list
         SuperPassDesc sp = make_pass(kLoadFull, 0, kTileDigits, 0, H, merged);
         sp.ph[0].reduce = 1;
         sp.ph[0].out = 1;
-        sp.ph[0].chunk_mask = (ng >= 2) ? 0 : 0x18;
+        sp.ph[0].chunk_mask = 0x18;
         push(sp);
     }
     p.n_done = 0;

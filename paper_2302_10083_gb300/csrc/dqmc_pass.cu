@@ -7,35 +7,36 @@
 // group digits (a .. a+K-1) and 7-K inner digits (0 .. 6-K, contiguous rows)
 // vary; every other high digit is fixed per tile.
 //
-// A thread works on a unit: the three tile rows that differ only in tile
-// digit 0 (three consecutive rows of the state).  They share every other
-// digit, so the neighbour arithmetic of a digit is done once for three rows,
-// and when tile digit 0 is a group digit (the bitmap pass) its Reduce is done
-// in registers.  Unit u holds tile rows 3u .. 3u+2; its digits are tile
-// digits 1..6.
-//
 // Per tile:
-//   load   the first pass reads truth-table words (tt_pass_kernel); the others
-//          copy the units whose group digits are 0/1 (Merge input) or all
-//          units into shared memory: cp.async, or bulk copies (TMA) on an
-//          mbarrier in the bitmap pass, whose tile is contiguous;
-//   Merge  the group digits one after another (Merge of Section 4.1: the
-//          '*' row becomes the AND of its 0 row and 1 row; '*' rows of an
-//          unmerged digit are zero in the state, so assignment equals the
-//          paper's OR);
-//   Reduce the group digits and the pass's chunk digits, every row read from
-//          the tile as merged (Reduce of Section 4.1: a cell loses its bit
-//          when its '*' neighbour in a reduced digit is set).  Reducing digits
-//          in groups, each group reading the state the previous groups left,
-//          gives the paper's result: a cube with an implicant one-digit
-//          extension is cleared in the first group that holds such a digit
-//          (the extension is still set then: clearing it would need an
-//          extension of the cube in an earlier group), and primes are never
-//          cleared;
+//   load   the first pass reads truth-table words (tt_pass_kernel); the
+//          others copy the rows whose group digits are 0/1 (Merge input) or
+//          every row into shared memory: cp.async of 16-byte pieces, or, in
+//          the bitmap pass, whose tile is contiguous, TMA bulk copies issued
+//          by one thread on an mbarrier whose wait is bounded;
+//   Merge  the group digits (Merge of Section 4.1: the '*' row becomes the
+//          AND of its 0 row and 1 row; '*' rows of an unmerged digit are zero
+//          in the state, so assignment equals the paper's OR);
+//   Reduce the group digits, then each row's chunk digits (Reduce of Section
+//          4.1: a cell loses its bit when its '*' neighbour in a reduced digit
+//          is set).  Reducing digits in groups, each group reading the state
+//          the previous groups left, gives the paper's result: a cube with an
+//          implicant one-digit extension is cleared in the first group that
+//          holds such a digit (the extension is still set then: clearing it
+//          would need an extension of the cube in an earlier group), and
+//          primes are never cleared;
 //   store  rows back to the state, or, in the last pass, the dense bitmap
 //          (each warp funnel-shifts its 96 rows into their own, no longer
 //          needed, slots of the tile), the count, and the (mask, value) list
 //          placed by a decoupled look-back over the tiles in rho order.
+//
+// Two kernels:
+//   mr_pass_kernel   the last Merge pass and the Reduce passes: the tile
+//                    row-major in shared memory, Merge and Reduce several
+//                    digits at a time in register blocks (dqmc_steps.cuh);
+//   unit_pass_kernel the Merge-only passes (a thread per unit: the three tile
+//                    rows that differ only in tile digit 0, one digit per
+//                    step) and the bitmap pass (row-major tile, Reduce in
+//                    register blocks, then the per-region bitmap and list).
 //
 // Every global index is checked against its buffer before the access (ck):
 // a bad one is recorded in the error word and the access skipped.
@@ -1177,8 +1178,6 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
             e = (ph.K == kTileDigits && ph.a == 0)
                     ? launch_tiles(tt_pass_kernel, (size_t)kTileRows * kChunkBytes, a, tiles, stream)
                     : cudaErrorInvalidValue;
-        else if (ph.out && ph.K == kTileDigits && ph.a == 0 && ph.chunk_mask == 0)
-            e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0>(a, tiles, stream);
         else if (ph.out && ph.K == kTileDigits && ph.a == 0 && ph.chunk_mask == 0x18)
             e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0x18>(a, tiles, stream);
         else if (ph.out)
@@ -1189,8 +1188,8 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
             e = dispatch_mr<0x07, true>(ph.K, a, tiles, stream);
         else if (ph.merge && !ph.reduce && ph.chunk_mask == 0)
             e = dispatch_group<kLoadSparse, kModeMerge, 0>(ph.K, a, tiles, stream);
-        else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x1f)
-            e = dispatch_mr<0x1f, false>(ph.K, a, tiles, stream);
+        else if (!ph.merge && ph.reduce && ph.chunk_mask == 0x07)
+            e = dispatch_mr<0x07, false>(ph.K, a, tiles, stream);
         else if (!ph.merge && ph.reduce && ph.chunk_mask == 0)
             e = dispatch_mr<0, false>(ph.K, a, tiles, stream);
         else
