@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--ref-n", type=int, default=REF_SAMPLE_N,
+                    help="--impl reference: the n of the function the oracle sweeps per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
@@ -79,6 +81,18 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (every rank gets it): a step time taken
+    on each rank becomes the job's step time."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -185,7 +199,7 @@ def run_reference(args, rank, world):
         return 0
     import oracle
     from paper_2302_10083_gb300 import synth
-    n = REF_SAMPLE_N
+    n = args.ref_n
     on, _ = synth.random_function(n, 1, P_ON)
     for _ in range(args.warmup):
         oracle.sweep(n, on)
@@ -288,11 +302,7 @@ def run_ours(args, rank, world, local):
         for p in range(npass):
             per_pass[p] += prev.elapsed_time(evs[k][p]) if p == 0 else evs[k][p - 1].elapsed_time(evs[k][p])
     per_pass = [x / K for x in per_pass]
-    ms = total_ms / K
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(total_ms / K, world, f"cuda:{local}")
     clocks = None
     if sampler:
         time.sleep(0.3)
@@ -331,7 +341,7 @@ def run_ours(args, rank, world, local):
     }
 
     if not args.no_e2e:
-        result["e2e"] = e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier, dist)
+        result["e2e"] = e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -341,7 +351,7 @@ def run_ours(args, rank, world, local):
     return 0
 
 
-def e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier, dist):
+def e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier):
     """Same metric through the host entry point dqmc_list: truth table from
     pinned host memory in, (mask, value) list and count out to pinned host
     memory, all inside the timed region."""
@@ -366,11 +376,7 @@ def e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier, di
         st = L.dqmc_list(n, on_p, None, out_p, cap, ctypes.byref(cnt))
         if st != 0:
             raise dqmc.DqmcError(st, "dqmc_list")
-    dt = (time.perf_counter() - t0) / steps
-    if world > 1:
-        t = torch.tensor([dt], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks((time.perf_counter() - t0) / steps, world, f"cuda:{local}")
     dqmc.dqmc_release()
     return {"value": world * 3 ** n / dt, "unit": "cubes/s", "ms_per_step": 1e3 * dt, "steps": steps,
             "h2d_bytes_per_step": int(on.size), "d2h_bytes_per_step": int(8 * cnt.value + 8),
