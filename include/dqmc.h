@@ -108,7 +108,9 @@ int dqmc_count(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
 int dqmc_list(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
               uint32_t *out_pairs, uint64_t cap, uint64_t *out_count);
 
-/* Free the device memory cached by the host API on the current device. */
+/* Free the device buffers cached by the host API on the current device.  It
+ * waits for a host call in progress on that device; a later call allocates
+ * them again.  The device's stream and count word stay until exit. */
 void dqmc_release(void);
 
 /* ---------------------------------------------------------------- device API

@@ -613,17 +613,19 @@ extern "C" void dqmc_release(void)
         cudaGetLastError();
         return;
     }
-    std::lock_guard<std::mutex> g(g_cache_mu);
-    DeviceCache *c = g_cache[dev];
-    if (!c) return;
+    DeviceCache *c = nullptr;
     {
-        std::lock_guard<std::mutex> g2(c->mu);
-        for (int i = 0; i < 5; ++i)
-            if (c->buf[i]) cudaFree(c->buf[i]);
-        if (c->d_count) cudaFree(c->d_count);
-        if (c->h_count) cudaFreeHost(c->h_count);
-        if (c->stream) cudaStreamDestroy(c->stream);
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        c = g_cache[dev];
     }
-    delete c;
-    g_cache[dev] = nullptr;
+    if (!c) return;
+    // Only the buffers go: a host call on another thread may hold this entry
+    // and be waiting for its lock, so the entry itself (its stream and count
+    // words, a few bytes) stays for the life of the process.
+    std::lock_guard<std::mutex> g2(c->mu);
+    for (int i = 0; i < 5; ++i) {
+        if (c->buf[i]) cudaFree(c->buf[i]);
+        c->buf[i] = nullptr;
+        c->cap[i] = 0;
+    }
 }
