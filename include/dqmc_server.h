@@ -11,11 +11,17 @@
  * their bitmap.  Admitted jobs run while others are still running:
  *   * jobs with n <= 14 that are waiting together are swept by one batched
  *     launch per n (whole functions in shared memory, the launch shapes of
- *     dqmc_batch_get_config; a cluster of three CTAs per function at n = 14);
+ *     dqmc_batch_get_config; a cluster of nine CTAs per function at n = 14,
+ *     so that no job needs a workspace);
  *   * jobs with n >= 15 run on their own CUDA stream (several at a time).
  * When a job's kernels are done, its state and tables are freed at once and
  * the next jobs are admitted; its bitmap stays in device memory until the
  * client frees the job (or at once, for DQMC_JOB_DISCARD_BITMAP).
+ *
+ * Errors: if a launch cannot be enqueued, the server keeps that CUDA error
+ * (DQMC_ECUDA or DQMC_ENOMEM) and returns it from submit, query, wait and
+ * destroy; the jobs of that launch and every job still queued are marked
+ * done with no result, and nothing more is started.
  */
 #ifndef DQMC_SERVER_H
 #define DQMC_SERVER_H

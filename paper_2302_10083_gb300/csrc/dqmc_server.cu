@@ -495,6 +495,17 @@ void dqmc_server::run()
             std::unique_lock<std::mutex> lk(mu);
             cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return dirty || stop; });
             dirty = false;
+            if (sticky && !queue.empty()) {
+                // a launch failed: nothing more is started, the queued jobs
+                // end with the error (their waiters see it)
+                const uint64_t t = now_ns();
+                for (uint64_t id : queue) {
+                    jobs[id].state = DQMC_JOB_DONE;
+                    jobs[id].t_done = t;
+                }
+                queue.clear();
+                cv.notify_all();
+            }
             if (stop && queue.empty() && running_groups == 0) break;
             todo = admit();
         }
