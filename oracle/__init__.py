@@ -10,6 +10,8 @@ use and wraps it with ctypes:
 
 * :func:`sweep` -- Algorithm 3 (Section 4.1), one byte per cube, returns the
   final state (nonzero = prime implicant).
+* :func:`sweep_packed`, :func:`packed_bitmap` -- the same passes with one bit
+  per cube, for n whose byte state does not fit in host memory.
 * :func:`bitmap`, :func:`count`, :func:`pairs` -- the three outputs: dense
   LSB-first bitmap indexed by rho, the number of primes, the (mask, value) list
   in ascending rho.
@@ -81,6 +83,11 @@ def lib():
             L.oracle_is_implicant.argtypes = [ctypes.c_int, u8p, u8p, ctypes.c_uint64]
             L.oracle_is_prime.restype = ctypes.c_int
             L.oracle_is_prime.argtypes = [ctypes.c_int, u8p, u8p, ctypes.c_uint64]
+            L.oracle_sweep_packed.restype = None
+            L.oracle_sweep_packed.argtypes = [ctypes.c_int, u8p, u8p, ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.c_int]
+            L.oracle_packed_bitmap.restype = None
+            L.oracle_packed_bitmap.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), u8p]
             L.oracle_is_prime_many.restype = None
             L.oracle_is_prime_many.argtypes = [ctypes.c_int, u8p, u8p,
                                                ctypes.POINTER(ctypes.c_uint64),
@@ -123,6 +130,25 @@ def sweep(n: int, on, dc=None, threads: int = 0, return_counts: bool = False):
     if return_counts:
         return S, (int(counts[0]), int(counts[1]))
     return S
+
+
+def sweep_packed(n: int, on, dc=None, threads: int = 0) -> np.ndarray:
+    """Algorithm 3 with one bit per cube (ceil(3^n/64) uint64 words, cube rho
+    at bit rho % 64 of word rho // 64): the same passes as :func:`sweep` in a
+    ninth of the host memory, for the sizes whose byte state does not fit."""
+    on = _tt(on, n)
+    dc = _tt(dc, n)
+    S = np.empty((3 ** n + 63) // 64, dtype=np.uint64)
+    lib().oracle_sweep_packed(n, _p(on), _p(dc), S.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                              int(threads))
+    return S
+
+
+def packed_bitmap(n: int, S: np.ndarray) -> np.ndarray:
+    """The dense LSB-first bitmap (ceil(3^n/8) bytes) of a packed state."""
+    out = np.empty((3 ** n + 7) // 8, dtype=np.uint8)
+    lib().oracle_packed_bitmap(n, S.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _p(out))
+    return out
 
 
 def bitmap(n: int, S: np.ndarray) -> np.ndarray:

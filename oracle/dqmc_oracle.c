@@ -25,6 +25,8 @@
  *   Reduce(c0, c1, c*) -> (c0 AND NOT c*, c1 AND NOT c*, c*)
  * The triples of one digit are independent (Section 4.1), so they are split
  * across OpenMP threads; nothing else is reordered or fused.
+ * oracle_sweep_packed runs the same passes with one bit per cube, for sizes
+ * whose byte state does not fit in host memory.
  *
  * oracle_is_implicant / oracle_is_prime are the plain definitions, evaluated
  * for one cube by enumerating its minterms; they serve as the pointwise check at
@@ -240,4 +242,102 @@ void oracle_is_prime_many(int n, const uint8_t *on, const uint8_t *dc,
     #pragma omp parallel for schedule(dynamic, 64)
     for (uint64_t k = 0; k < count; ++k)
         out[k] = (uint8_t)oracle_is_prime(n, on, dc, rhos[k]);
+}
+
+/*
+ * Packed mode: the same Algorithm 3 with one BIT per cube, for sizes whose
+ * byte state does not fit in host memory.  S holds ceil(3^n/64) words; cube
+ * rho is bit rho%64 of word rho/64.  Within one digit i every triple is
+ * independent (Section 4.1), and a pass writes only one kind of cell: Merge
+ * writes the cells whose digit i is *, reading their 0 and 1 siblings; Reduce
+ * writes the cells whose digit i is 0 or 1, reading their * sibling.  So the
+ * words are split across threads, each thread updates the cells of its own
+ * words, and every cell it reads is one that no thread writes in that pass.
+ */
+/* Words are read and written whole with relaxed atomics: a word another
+ * thread is storing keeps the bits read here (only its other kind of cell
+ * changes), and the atomics make that well defined. */
+static int pk_get(const uint64_t *S, uint64_t r)
+{
+    return (int)((__atomic_load_n(&S[r >> 6], __ATOMIC_RELAXED) >> (r & 63)) & 1u);
+}
+
+/* Digit i (weight d = 3^(i-1)) of cell r, and the position of r inside its
+ * run of d cells with that digit. */
+static void pk_digit_at(uint64_t r, uint64_t d, unsigned *digit, uint64_t *pos)
+{
+    *digit = (unsigned)((r / d) % 3u);
+    *pos = r % d;
+}
+
+void oracle_sweep_packed(int n, const uint8_t *on, const uint8_t *dc, uint64_t *S, int threads)
+{
+    const uint64_t N = oracle_pow3(n);
+    const uint64_t W = (N + 63) / 64;
+    const uint64_t T = (uint64_t)1 << n;
+    set_threads(threads);
+
+    /* Load the input: bit rho(t) = I(t) for every minterm t. */
+    memset(S, 0, W * sizeof(uint64_t));
+    for (uint64_t t = 0; t < T; ++t)
+        if (support_bit(on, dc, t)) {
+            const uint64_t r = rho_of_minterm(n, t);
+            S[r >> 6] |= (uint64_t)1 << (r & 63);
+        }
+
+    /* MergeAll: for i = 1..n, every * cell u |= (its 0 sibling) & (its 1 sibling). */
+    uint64_t d = 1;
+    for (int i = 1; i <= n; ++i) {
+        const uint64_t dd = d;
+        #pragma omp parallel for schedule(static)
+        for (uint64_t w = 0; w < W; ++w) {
+            const uint64_t r0 = 64 * w, r1 = (r0 + 64 < N) ? r0 + 64 : N;
+            unsigned digit;
+            uint64_t pos;
+            pk_digit_at(r0, dd, &digit, &pos);
+            uint64_t word = __atomic_load_n(&S[w], __ATOMIC_RELAXED);
+            for (uint64_t r = r0; r < r1; ++r) {
+                if (digit == 2u && pk_get(S, r - 2 * dd) && pk_get(S, r - dd))
+                    word |= (uint64_t)1 << (r - r0);
+                if (++pos == dd) {   /* next cell starts the next run of digit i */
+                    pos = 0;
+                    digit = (digit + 1u) % 3u;
+                }
+            }
+            __atomic_store_n(&S[w], word, __ATOMIC_RELAXED);
+        }
+        d *= 3u;
+    }
+
+    /* ReduceAll: same digits, same order: every 0 or 1 cell &= !(its * sibling). */
+    d = 1;
+    for (int i = 1; i <= n; ++i) {
+        const uint64_t dd = d;
+        #pragma omp parallel for schedule(static)
+        for (uint64_t w = 0; w < W; ++w) {
+            const uint64_t r0 = 64 * w, r1 = (r0 + 64 < N) ? r0 + 64 : N;
+            unsigned digit;
+            uint64_t pos;
+            pk_digit_at(r0, dd, &digit, &pos);
+            uint64_t word = __atomic_load_n(&S[w], __ATOMIC_RELAXED);
+            for (uint64_t r = r0; r < r1; ++r) {
+                if (digit != 2u && pk_get(S, r + (2u - digit) * dd))
+                    word &= ~((uint64_t)1 << (r - r0));
+                if (++pos == dd) {
+                    pos = 0;
+                    digit = (digit + 1u) % 3u;
+                }
+            }
+            __atomic_store_n(&S[w], word, __ATOMIC_RELAXED);
+        }
+        d *= 3u;
+    }
+}
+
+/* The packed state as the dense LSB-first bitmap: byte k holds cubes 8k..8k+7. */
+void oracle_packed_bitmap(int n, const uint64_t *S, uint8_t *out)
+{
+    const uint64_t bytes = (oracle_pow3(n) + 7) / 8;
+    for (uint64_t k = 0; k < bytes; ++k)
+        out[k] = (uint8_t)(S[k >> 3] >> (8 * (k & 7)));
 }

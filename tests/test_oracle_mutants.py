@@ -2,7 +2,8 @@
 
 Each case compiles a copy of ``oracle/dqmc_oracle.c`` with one planted mistake
 (a dropped term, a wrong index, a wrong operator, a skipped digit, an ignored
-don't-care set) and checks that brute force (Section 2 definitions) or a worked
+don't-care set; in the packed mode a wrong sibling, a digit that does not
+wrap, a skipped word, a wrong byte order) and checks that brute force (Section 2 definitions) or a worked
 example rejects it.  Everything runs on the CPU.
 """
 import ctypes
@@ -31,9 +32,20 @@ MUTANTS = {
     "reduce_reads_wrong_cell": ("const uint8_t z = S[iu];", "const uint8_t z = S[it];"),
 }
 
+# mistakes in the packed (bit per cube) mode
+PACKED_MUTANTS = {
+    "packed_merge_same_sibling": ("pk_get(S, r - 2 * dd) && pk_get(S, r - dd)",
+                                  "pk_get(S, r - 2 * dd) && pk_get(S, r - 2 * dd)"),
+    "packed_reduce_wrong_sibling": ("pk_get(S, r + (2u - digit) * dd)", "pk_get(S, r + (1u + digit) * dd)"),
+    "packed_digit_no_wrap": ("digit = (digit + 1u) % 3u;", "digit = digit + 1u;"),
+    "packed_last_word_skipped": ("for (uint64_t w = 0; w < W; ++w) {", "for (uint64_t w = 0; w < W - 1; ++w) {"),
+    "packed_bitmap_byte_order": ("(uint8_t)(S[k >> 3] >> (8 * (k & 7)))",
+                                 "(uint8_t)(S[k >> 3] >> (8 * (7 - (k & 7))))"),
+}
+
 
 def build_mutant(tmp_path, name):
-    old, new = MUTANTS[name]
+    old, new = {**MUTANTS, **PACKED_MUTANTS}[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, name
     src = src.replace(old, new, 1)
@@ -47,6 +59,23 @@ def build_mutant(tmp_path, name):
     L.oracle_sweep.argtypes = [ctypes.c_int, u8p, u8p, u8p, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_uint64)]
     L.oracle_sweep.restype = None
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    L.oracle_sweep_packed.argtypes = [ctypes.c_int, u8p, u8p, u64p, ctypes.c_int]
+    L.oracle_sweep_packed.restype = None
+    L.oracle_packed_bitmap.argtypes = [ctypes.c_int, u64p, u8p]
+    L.oracle_packed_bitmap.restype = None
+
+    if name in PACKED_MUTANTS:
+        def sweep_packed(n, on, dc=None):
+            S = np.empty((3 ** n + 63) // 64, dtype=np.uint64)
+            bm = np.empty((3 ** n + 7) // 8, dtype=np.uint8)
+            on = np.ascontiguousarray(on, dtype=np.uint8)
+            dcp = None if dc is None else np.ascontiguousarray(dc, dtype=np.uint8)
+            L.oracle_sweep_packed(n, on.ctypes.data_as(u8p), None if dcp is None else dcp.ctypes.data_as(u8p),
+                                  S.ctypes.data_as(u64p), 2)
+            L.oracle_packed_bitmap(n, S.ctypes.data_as(u64p), bm.ctypes.data_as(u8p))
+            return bf.bool_from_bitmap(bm, n)
+        return sweep_packed
 
     def sweep(n, on, dc=None):
         S = np.empty(3 ** n, dtype=np.uint8)
@@ -85,4 +114,18 @@ def test_unmutated_copy_passes(tmp_path):
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(tmp_path, name):
+    assert not pins_pass(build_mutant(tmp_path, name)), name
+
+
+def test_unmutated_packed_copy_passes(tmp_path):
+    old = PACKED_MUTANTS["packed_digit_no_wrap"][0]
+    PACKED_MUTANTS["_packed_identity"] = (old, old)
+    try:
+        assert pins_pass(build_mutant(tmp_path, "_packed_identity"))
+    finally:
+        del PACKED_MUTANTS["_packed_identity"]
+
+
+@pytest.mark.parametrize("name", sorted(PACKED_MUTANTS))
+def test_packed_mutant_is_caught(tmp_path, name):
     assert not pins_pass(build_mutant(tmp_path, name)), name

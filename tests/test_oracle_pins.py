@@ -371,3 +371,45 @@ def test_expected_prime_count_band():
         counts.append(oracle.count(n, oracle.sweep(n, on)))
     e = bf.expected_primes(n, p)
     assert abs(np.mean(counts) - e) / e < 0.03
+
+
+# ---------------------------------------------------------------- packed mode
+
+def packed_cells(n, on, dc=None, threads=0):
+    return bf.bool_from_bitmap(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc, threads)), n)
+
+
+@pytest.mark.parametrize("n", list(range(0, 9)))
+def test_packed_bruteforce_random(n):
+    """Packed mode against the definitions (Section 2) by enumeration, n <= 8,
+    with and without don't-cares."""
+    for seed in range(1, 4):
+        for p, p_dc in ((0.4, 0.0), (0.7, 0.15), (0.92, 0.0)):
+            on, dc = synth.random_function(n, seed, p, p_dc)
+            want = bf.primes(n, bf.support_of(n, on, dc))
+            assert np.array_equal(packed_cells(n, on, dc), want), (n, seed, p)
+
+
+@pytest.mark.parametrize("n,W", [(9, {5, 6, 7, 8, 9}), (12, {1, 2, 6, 7, 8, 12}), (13, set(range(1, 14, 2)))])
+def test_packed_symmetric_closed_form(n, W):
+    """Symmetric functions in closed form at sizes where runs of a digit are
+    both shorter and longer than a 64-cube word."""
+    cells = packed_cells(n, bf.bitmap_from_bool(bf.symmetric_support(n, W)))
+    assert np.array_equal(cells, bf.symmetric_prime_cells(n, W))
+
+
+def test_packed_constant_one_and_tail():
+    """f = 1 (Section 3): only the all-* cube; the bits past 3^n stay 0."""
+    for n in (4, 11):
+        bm = oracle.packed_bitmap(n, oracle.sweep_packed(n, np.full(synth.tt_bytes(n), 0xFF, dtype=np.uint8)))
+        cells = np.nonzero(np.unpackbits(bm, bitorder="little"))[0].tolist()
+        assert cells == [3 ** n - 1]
+
+
+@pytest.mark.parametrize("n", [10, 13, 15])
+def test_packed_equals_byte_sweep(n):
+    """The two storage modes give the same primes, on one thread and on all."""
+    on, dc = synth.random_function(n, 40 + n, 0.8, 0.1)
+    want = oracle.bitmap(n, oracle.sweep(n, on, dc))
+    assert np.array_equal(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc, threads=1)), want)
+    assert np.array_equal(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc)), want)
