@@ -1,10 +1,12 @@
 """GPU parity: libdqmc.so (through its C ABI) against the CPU oracle.
 
 Bit-exact on the prime bitmap, the count and the (mask, value) list.  Small
-and medium n are compared element by element; n = 24 (the full-size
-workload) is checked on sampled cells with the oracle's pointwise definition,
-on every sampled listed prime, and by the structural properties that hold at
-any size.
+and medium n are compared element by element (up to n = 21 against the
+byte-per-cube oracle; n = 22 against its bit-per-cube mode in
+test_zz_parity_n22_exact.py); n = 22 .. 25,
+with n = 24 the full-size workload, are also checked on sampled cells with the
+oracle's pointwise definition, on every sampled listed prime, and by the
+structural properties that hold at any size.
 """
 import numpy as np
 import pytest
@@ -194,8 +196,9 @@ def test_repeat_calls_identical():
 
 
 def test_n21_three_phase_pass_bit_exact():
-    """n = 21 is the smallest n whose Merge/Reduce pass over the top digits runs
-    three phases on L2-resident super-blocks: bit-exact against the byte oracle."""
+    """n = 21 (two groups of high digits above the tile, so every kind of pass:
+    first, sparse Merge, last Merge + Reduce, middle Reduce, bitmap) with the
+    bitmap and list bit-exact against the byte oracle (10.5 GB of state)."""
     on, dc = synth.random_function(21, 6, 0.8, 0.05)
     check_all(21, on, dc)
 
