@@ -94,3 +94,37 @@ def test_unit_rows_loads_and_merge_items(a, K, B):
     assert have == set(range(units))
     written = {u for u in range(units) if 2 in group_of(u)}
     assert written == set(range(units)) - loaded
+
+
+def row_pass_shapes():
+    shapes = set()
+    for n in (13, 16, 19, 21, 24, 25):
+        for p in dqmc.dqmc_plan_json(n)["passes"]:
+            ph = p["phases"][0]
+            if ph["B"] >= 1 and ph["load"] in ("sparse", "full"):
+                shapes.add((ph["a"], ph["K"], ph["B"], ph["load"]))
+    return sorted(shapes)
+
+
+@pytest.mark.parametrize("a,K,B,load", row_pass_shapes())
+def test_row_pass_rows_and_loads(a, K, B, load):
+    """The Merge + Reduce and Reduce passes hold the tile row-major: tile row
+    e + 3^B g (e: inner digits, g: group digits) is state row base + e + g 3^a,
+    so the tile's base-3 digits are the inner digits, then the group digits, as
+    the block steps assume.  The sparse load takes the rows with 0/1 group
+    digits, each once."""
+    RE = 3 ** B
+    base = 777
+    seen = set()
+    for ri in range(3 ** TILE):
+        g, e = divmod(ri, RE)
+        row = base + e + g * 3 ** a
+        d = digits_of(ri, TILE)
+        assert row == base + sum(x * 3 ** i for i, x in enumerate(d[:B])) + \
+            sum(x * 3 ** (a + i) for i, x in enumerate(d[B:]))
+        assert row not in seen
+        seen.add(row)
+    if load == "sparse":
+        rows = [e + RE * spread3(gb, K) for gb in range(1 << K) for e in range(RE)]
+        assert len(set(rows)) == len(rows)
+        assert set(rows) == {ri for ri in range(3 ** TILE) if 2 not in digits_of(ri, TILE)[B:]}
