@@ -24,14 +24,31 @@ def _gpu():
 
 
 def _mem_available_bytes():
+    """Host memory this process can still use: MemAvailable, capped by the
+    cgroup's limit less its usage when one is set (inside a container
+    /proc/meminfo shows the whole machine)."""
+    avail = 0
     try:
         with open("/proc/meminfo") as f:
             for line in f:
                 if line.startswith("MemAvailable:"):
-                    return int(line.split()[1]) * 1024
+                    avail = int(line.split()[1]) * 1024
     except OSError:
-        pass
-    return 0
+        return 0
+    for limit_file, usage_file in (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                                   ("/sys/fs/cgroup/memory/memory.limit_in_bytes",
+                                    "/sys/fs/cgroup/memory/memory.usage_in_bytes")):
+        try:
+            with open(limit_file) as f:
+                limit = f.read().strip()
+            with open(usage_file) as f:
+                usage = int(f.read().strip())
+        except (OSError, ValueError):
+            continue
+        if limit.isdigit():
+            avail = min(avail, max(int(limit) - usage, 0))
+        break
+    return avail
 
 
 def test_n22_bit_exact_packed_oracle():
