@@ -105,8 +105,13 @@ def stream_out(glob, regions, R, part, parts, out_words, alloc_words):
             glob[w] = 0
 
 
-@pytest.mark.parametrize("n,parts", [(5, 1), (6, 1), (8, 1), (10, 1), (11, 1), (13, 1), (13, 3), (14, 3), (14, 9)])
-def test_function_bitmap_written_exactly(n, parts):
+@pytest.mark.parametrize("n,parts,first_direct", [(5, 1, False), (6, 1, False), (8, 1, False), (10, 1, False),
+                                                  (11, 1, False), (13, 1, False), (13, 3, False), (14, 3, False),
+                                                  (14, 9, False), (14, 3, True)])
+def test_function_bitmap_written_exactly(n, parts, first_direct):
+    """first_direct: one CTA doing the thirds in turn writes third 0 as a
+    stream that starts at bit 0 (whole words, its last one with the upper bits
+    0), before the masked stores of thirds 1 and 2."""
     rng = np.random.default_rng(n * 10 + parts)
     total_rows = 3 ** (n - 5)
     R = total_rows // parts
@@ -117,12 +122,13 @@ def test_function_bitmap_written_exactly(n, parts):
     for part in range(parts):
         rows = [row_words(cells[(part * R + r) * C3:(part * R + r + 1) * C3]) for r in range(R)]
         regions = pack(rows)
-        if parts == 1:                        # DIRECT: packed regions straight to the bitmap
+        if parts == 1 or (first_direct and part == 0):   # DIRECT: packed regions straight to the bitmap
             NP = (R * C3 + 31) // 32
             for j in range(NP):
                 glob[j] = regions[j // C3][j % C3]
-            for w in range(out_words, alloc_words):
-                glob[w] = 0
+            if parts == 1:
+                for w in range(out_words, alloc_words):
+                    glob[w] = 0
         else:
             stream_out(glob, regions, R, part, parts, out_words, alloc_words)
     want = np.packbits(cells, bitorder="little")
