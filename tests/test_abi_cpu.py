@@ -475,3 +475,28 @@ def test_batch_autotune_arguments_without_gpu():
     assert L.dqmc_batch_autotune(2, n_p, o_p, 256, None, 256, 256, o_p, 0, None, out) == dqmc.DQMC_EINVAL
     assert L.dqmc_batch_autotune(2, n_p, o_p, 256, None, 256, 256, o_p, 1001, None, out) == dqmc.DQMC_EINVAL
     assert L.dqmc_batch_autotune(2, None, o_p, 256, None, 256, 256, o_p, 3, None, out) == dqmc.DQMC_EINVAL
+
+
+# ---------------------------------------------------------------- Table 1 memory
+
+def test_state_size_matches_table1_ram_column():
+    """Table 1 (DenseQMC, density: any): the RAM column is the in-place state
+    of 3^(n-5) blocks of 256 bits (h = 5 digits per block), at the printed
+    precision, for n = 16 .. 27.  The library's plan keeps exactly that state,
+    one 32-byte row per block, up to n = 25 (the largest n it takes); its
+    device workspace adds under 1% (a control block and the list's scan
+    counters)."""
+    unit = {"MiB": 2 ** 20, "GiB": 2 ** 30, "TiB": 2 ** 40}
+    rows = []
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_dense_ram.txt")):
+        if line.strip() and not line.startswith("#"):
+            n, val, u = line.split()
+            rows.append((int(n), val, u))
+    assert [n for n, _, _ in rows] == list(range(16, 28))
+    for n, val, u in rows:
+        decimals = len(val.split(".")[1]) if "." in val else 0
+        state = 3 ** (n - 5) * 32
+        assert round(state / unit[u], decimals) == float(val), (n, state / unit[u], val)
+        if n <= 25:
+            assert dqmc.dqmc_plan_json(n)["state_rows"] * 32 == state
+            assert state <= dqmc.dqmc_workspace_bytes(n) <= state * 1.01
