@@ -413,4 +413,3 @@ def test_packed_equals_byte_sweep(n):
     want = oracle.bitmap(n, oracle.sweep(n, on, dc))
     assert np.array_equal(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc, threads=1)), want)
     assert np.array_equal(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc)), want)
-
