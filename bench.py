@@ -50,6 +50,7 @@ P_ON = 0.85
 REF_SAMPLE_N = 19       # --impl reference: one oracle sweep of this size per step
 CPU_BASELINE_N = 20     # cpu_baseline: one oracle sweep of this size
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e, nominal (about 8 TB/s)
 
 
 def parse_args():
@@ -334,6 +335,8 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes_per_launch": dom_bytes},
         "path_roofline": {"b_roof_bytes": b_roof, "achieved_gbs": b_roof / (ms / 1e3) / 1e9,
                           "frac_of_peak": b_roof / (ms / 1e3) / 1e9 / peak,
+                          "frac_of_nominal": b_roof / (ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
+                          "nominal_gbs": NOMINAL_HBM_GBS,
                           "note": "B_roof = 2^n/8 + 3*ceil(3^n/8): read input, write merged state, read it, write primes"},
         "per_kernel_ms": {names[p]: per_pass[p] for p in range(npass)},
         "gpu_launches": K * npass,
