@@ -21,12 +21,24 @@ extern "C" {
 /* Writes a NUL-terminated JSON description of the plan for n variables into
  * buf (at most cap bytes, truncated if needed) and returns the full length of
  * the JSON text, or DQMC_EINVAL (-1) for n > DQMC_MAX_N.  buf may be NULL when
- * cap is 0 (to query the length).  Fields: n, C (chunk digits, min(n, 5)),
- * H (high digits), state_rows (32-byte rows of device state; 0 when the whole
- * function fits one tile) and passes[] with kind ("first" | "merge" |
- * "reduce"), K (group digits a .. a+K-1 among the high digits), B (inner
- * digits 0 .. B-1 carried for contiguous rows), top_binary, fuse_reduce,
- * chunk_reduce, write_out, tiles, n_mid, w_g, w_top. */
+ * cap is 0 (to query the length).  Fields:
+ *   n; C (chunk digits, min(n, 5)); H (high digits, n - C);
+ *   state_rows (32-byte rows of device state; 0 when one tile holds the whole
+ *     function); out_tiles (tiles of the bitmap pass);
+ *   passes[], one per kernel launch, each with
+ *     kind: "whole" (n <= 12, one CTA per function) or "super" (a streaming
+ *       pass over tiles of 3^7 rows);
+ *     n_sb: tiles; sb: [digit, radix] of each high digit fixed per tile, in the
+ *       order the tile index enumerates them (radix 2 while the digit is not
+ *       merged yet, else 3);
+ *     window, step_size, n_steps, groups: the launch shape (one launch of
+ *       n_sb tiles: window = step_size = n_sb, n_steps = groups = 1);
+ *     phases[] (one): load ("tt": truth table, "sparse": the rows whose group
+ *       digits are 0/1, "full": every row); a, K (group digits a .. a+K-1);
+ *       B (inner digits 0 .. B-1, carried for contiguous rows); merge, reduce
+ *       (0/1: the pass merges / reduces its group digits); chunk_mask (bit i:
+ *       the pass reduces chunk digit i); out (the pass writes the bitmap, the
+ *       count and the list); tiles; fix (unused, empty). */
 int dqmc_plan_json(uint32_t n, char *buf, uint64_t cap);
 
 /* Number of passes (kernel launches of the sweep) for n variables, or
