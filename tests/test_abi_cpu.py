@@ -500,3 +500,24 @@ def test_state_size_matches_table1_ram_column():
         if n <= 25:
             assert dqmc.dqmc_plan_json(n)["state_rows"] * 32 == state
             assert state <= dqmc.dqmc_workspace_bytes(n) <= state * 1.01
+
+
+@pytest.mark.parametrize("n", [0, 8, 12, 13, 21, 24, 25])
+def test_plan_json_fields_as_documented(n):
+    """dqmc_plan_json writes exactly the fields include/dqmc_plan.h lists."""
+    p = dqmc.dqmc_plan_json(n)
+    assert set(p) == {"n", "C", "H", "state_rows", "out_tiles", "passes"}
+    assert p["n"] == n and p["C"] == min(n, 5) and p["H"] == n - p["C"]
+    assert len(p["passes"]) == dqmc.dqmc_plan_passes(n)
+    for q in p["passes"]:
+        assert q["kind"] in ("whole", "super")
+        want = {"kind", "n_sb", "window", "sb", "phases"} | (
+            {"step_size", "n_steps", "groups"} if q["kind"] == "super" else set())
+        assert set(q) == want
+        assert len(q["phases"]) == 1
+        ph = q["phases"][0]
+        assert set(ph) == {"load", "K", "B", "a", "merge", "reduce", "chunk_mask", "out", "tiles", "fix"}
+        assert ph["load"] in ("tt", "sparse", "full") and ph["fix"] == []
+        if q["kind"] == "super":
+            assert q["window"] == q["step_size"] == q["n_sb"] and q["n_steps"] == q["groups"] == 1
+    assert (p["state_rows"] == 0) == (p["passes"][0]["kind"] == "whole")
