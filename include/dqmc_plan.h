@@ -31,8 +31,9 @@ extern "C" {
  *     n_sb: tiles; sb: [digit, radix] of each high digit fixed per tile, in the
  *       order the tile index enumerates them (radix 2 while the digit is not
  *       merged yet, else 3);
- *     window, step_size, n_steps, groups: the launch shape (one launch of
- *       n_sb tiles: window = step_size = n_sb, n_steps = groups = 1);
+ *     window (both kinds), step_size, n_steps, groups ("super" only): the
+ *       launch shape (one launch of n_sb tiles: window = step_size = n_sb,
+ *       n_steps = groups = 1);
  *     phases[] (one): load ("tt": truth table, "sparse": the rows whose group
  *       digits are 0/1, "full": every row); a, K (group digits a .. a+K-1);
  *       B (inner digits 0 .. B-1, carried for contiguous rows); merge, reduce
