@@ -84,8 +84,10 @@ typedef struct {
  *   d_out_count    nfun uint64, f's number of prime implicants;
  *   d_out_bitmaps  the bitmap slots, 16-byte aligned.
  *
- * The library owns the workspace (device states of the n = 13, 14
- * functions on the TILES path, per-class control blocks, the function tables) and the graph;
+ * The library owns the workspace (the function tables; device states and
+ * control blocks of the n = 13, 14 functions on the TILES path; when the batch
+ * has n = 14 functions, one 210 KB slot per SM for the one-CTA thirds) and
+ * the graph;
  * both stay allocated until dqmc_batch_release.  Calls must not overlap on
  * the device (they share that workspace): order them on one stream, or
  * synchronise between them.  The call returns once the graph is enqueued;
@@ -100,8 +102,10 @@ int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, con
                    void *stream);
 
 /* Bytes of device workspace a batch with these n's takes (function tables,
- * control blocks, states of the n = 13, 14 functions).  0 if an n is out of
- * range. */
+ * control blocks and states of the n = 13, 14 functions on the TILES path,
+ * the n = 14 scratch slots), sized for the configurations set now and the
+ * current device's SM count (160 slots when no device answers).  0 if an n
+ * is out of range. */
 uint64_t dqmc_batch_workspace_bytes(uint32_t nfun, const uint32_t *n);
 
 /* The configuration used for functions of n variables (process-wide; the
