@@ -81,7 +81,8 @@ uint64_t dqmc_bitmap_alloc_bytes(uint32_t n);
 
 /* Device workspace needed by dqmc_primes_dev / dqmc_list_dev for this n
  * (0 for n > DQMC_MAX_N).  It holds the padded ternary state (3^(n-5) rows of
- * 32 bytes for n >= 13) and the list scan counters. */
+ * 32 bytes for n >= 13), a control block (error word, tile tickets, one
+ * look-back word per bitmap tile) and the list scan counters. */
 uint64_t dqmc_workspace_bytes(uint32_t n);
 
 /* ------------------------------------------------------------------ host API
@@ -137,10 +138,12 @@ int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc,
                   void *stream);
 
 /* Synchronises `stream`, then reports how the last sweep that used d_work
- * ended: DQMC_OK, or DQMC_ETIMEOUT when a bounded device wait of the sweep
- * (a tile waiting for the tiles it depends on, or the list's look-back) gave
- * up after one second and the outputs are not valid.  Device waits never
- * spin unbounded. */
+ * ended: DQMC_OK; DQMC_ETIMEOUT when a bounded device wait of the sweep (the
+ * bitmap pass waiting for its tile's bulk copies, or the list's look-back
+ * waiting for the tiles before it) gave up after one second; DQMC_ECUDA when
+ * a kernel found an index out of bounds and skipped the access.  In both
+ * error cases the outputs are not valid.  Device waits never spin
+ * unbounded. */
 int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *stream);
 
 /* For callers that cannot allocate device memory (an application whose own
