@@ -413,3 +413,41 @@ def test_packed_equals_byte_sweep(n):
     want = oracle.bitmap(n, oracle.sweep(n, on, dc))
     assert np.array_equal(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc, threads=1)), want)
     assert np.array_equal(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc)), want)
+
+
+# ---------------------------------------------------------------- stored digests
+
+def _make_digests():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_digests", os.path.join(GOLDEN, "make_digests.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_digest_script_matches_byte_oracle():
+    """The script that stores the large-n digests, run at small n, gives the
+    SHA-256 and count of the byte oracle's bitmap."""
+    import hashlib
+    md = _make_digests()
+    for n, seed, p, q in ((9, 2, 0.8, 0.05), (14, 1, 0.85, 0.0)):
+        h, c = md.digest(n, seed, p, q)
+        on, dc = synth.random_function(n, seed, p, q)
+        S = oracle.sweep(n, on, dc)
+        assert h == hashlib.sha256(oracle.bitmap(n, S).tobytes()).hexdigest()
+        assert c == oracle.count(n, S)
+
+
+def test_stored_digest_counts_near_expectation():
+    """Each stored count is within 1% of the exact expected prime count for
+    i.i.d. support of its density (ON, plus DC on the OFF minterms)."""
+    path = os.path.join(GOLDEN, "bitmap_digests.txt")
+    if not os.path.exists(path):
+        pytest.skip("no stored digests")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for n, seed, p_on, p_dc, count, h in rows:
+        n, p_on, p_dc, count = int(n), float(p_on), float(p_dc), int(count)
+        assert len(h) == 64 and int(h, 16) >= 0
+        e = bf.expected_primes(n, p_on + (1 - p_on) * p_dc)
+        assert abs(count - e) / e < 0.01, (n, count, e)

@@ -1,0 +1,88 @@
+"""n = 23 and n = 24 (the benchmark workload) bit-exact, at sizes where the
+oracle cannot run beside the test: the SHA-256 of libdqmc.so's prime bitmap
+(through the C ABI) and its prime count against the oracle's.  The oracle's
+values are in tests/golden/bitmap_digests.txt, written by
+tests/golden/make_digests.py, which runs only the oracle (its bit-per-cube
+sweep, Algorithm 3, Section 4.1) and the seeded input generator.  Equal
+digests mean equal bitmaps, bit for bit.  In a module collected after the
+others: the n = 24 bitmap takes 35 GB of host memory."""
+import hashlib
+import os
+
+import pytest
+
+from paper_2302_10083_gb300 import dqmc, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bitmap_digests.txt")
+
+
+def _cases():
+    out = {}
+    if os.path.exists(GOLDEN):
+        for line in open(GOLDEN):
+            if line.strip() and not line.startswith("#"):
+                n, seed, p_on, p_dc, count, h = line.split()
+                out[int(n)] = (int(seed), float(p_on), float(p_dc), int(count), h)
+    return out
+
+
+CASES = _cases()
+
+
+def _mem_available_bytes():
+    """MemAvailable, capped by the cgroup's limit less its usage when one is set."""
+    avail = 0
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        return 0
+    for limit_file, usage_file in (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                                   ("/sys/fs/cgroup/memory/memory.limit_in_bytes",
+                                    "/sys/fs/cgroup/memory/memory.usage_in_bytes")):
+        try:
+            with open(limit_file) as f:
+                limit = f.read().strip()
+            with open(usage_file) as f:
+                usage = int(f.read().strip())
+        except (OSError, ValueError):
+            continue
+        if limit.isdigit():
+            avail = min(avail, max(int(limit) - usage, 0))
+        break
+    return avail
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dqmc.lib()
+    yield
+    dqmc.dqmc_release()
+
+
+@pytest.mark.parametrize("n", [23, 24])
+def test_bitmap_digest_and_count(n):
+    if n not in CASES:
+        pytest.skip(f"no stored digest for n = {n}")
+    seed, p_on, p_dc, count, want = CASES[n]
+    A = (3 ** n + 7) // 8
+    if _mem_available_bytes() < A + (4 << 30):
+        pytest.skip(f"needs about {(A >> 30) + 4} GiB of available host memory")
+    free, _ = torch.cuda.mem_get_info()
+    need = dqmc.dqmc_workspace_bytes(n) + dqmc.dqmc_bitmap_alloc_bytes(n) + (1 << 30)
+    if free < need:
+        pytest.skip(f"needs {need >> 30} GiB of free device memory")
+    on, dc = synth.random_function(n, seed, p_on, p_dc)
+    got = dqmc.dqmc_primes(n, on, dc)
+    assert got.size == A
+    assert hashlib.sha256(memoryview(got)).hexdigest() == want
+    del got
+    assert dqmc.dqmc_count(n, on, dc) == count
