@@ -10,8 +10,9 @@ use and wraps it with ctypes:
 
 * :func:`sweep` -- Algorithm 3 (Section 4.1), one byte per cube, returns the
   final state (nonzero = prime implicant).
-* :func:`sweep_packed`, :func:`packed_bitmap` -- the same passes with one bit
-  per cube, for n whose byte state does not fit in host memory.
+* :func:`sweep_packed`, :func:`packed_bitmap`, :func:`packed_pairs` -- the
+  same passes with one bit per cube, for n whose byte state does not fit in
+  host memory, and its outputs.
 * :func:`bitmap`, :func:`count`, :func:`pairs` -- the three outputs: dense
   LSB-first bitmap indexed by rho, the number of primes, the (mask, value) list
   in ascending rho.
@@ -88,6 +89,9 @@ def lib():
                                               ctypes.c_int]
             L.oracle_packed_bitmap.restype = None
             L.oracle_packed_bitmap.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), u8p]
+            L.oracle_packed_list.restype = ctypes.c_uint64
+            L.oracle_packed_list.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64]
             L.oracle_is_prime_many.restype = None
             L.oracle_is_prime_many.argtypes = [ctypes.c_int, u8p, u8p,
                                                ctypes.POINTER(ctypes.c_uint64),
@@ -149,6 +153,15 @@ def packed_bitmap(n: int, S: np.ndarray) -> np.ndarray:
     out = np.empty((3 ** n + 7) // 8, dtype=np.uint8)
     lib().oracle_packed_bitmap(n, S.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _p(out))
     return out
+
+
+def packed_pairs(n: int, S: np.ndarray) -> np.ndarray:
+    """(mask, value) uint32 pairs of a packed state in ascending rho, shape (count, 2)."""
+    sp = S.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    c = int(lib().oracle_packed_list(n, sp, None, 0))
+    out = np.empty(2 * max(c, 1), dtype=np.uint32)
+    lib().oracle_packed_list(n, sp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), c)
+    return out[: 2 * c].reshape(c, 2)
 
 
 def bitmap(n: int, S: np.ndarray) -> np.ndarray:

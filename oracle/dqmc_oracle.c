@@ -341,3 +341,18 @@ void oracle_packed_bitmap(int n, const uint64_t *S, uint8_t *out)
     for (uint64_t k = 0; k < bytes; ++k)
         out[k] = (uint8_t)(S[k >> 3] >> (8 * (k & 7)));
 }
+
+/* The set cubes of a packed state in ascending rho, as (mask, value) pairs
+ * (oracle_encode); writes at most cap pairs, returns the number of set cubes. */
+uint64_t oracle_packed_list(int n, const uint64_t *S, uint32_t *pairs, uint64_t cap)
+{
+    const uint64_t W = (oracle_pow3(n) + 63) / 64;
+    uint64_t k = 0;
+    for (uint64_t w = 0; w < W; ++w)
+        for (uint64_t x = S[w]; x; x &= x - 1) {   /* the set bits of word w, lowest first */
+            const uint64_t rho = 64 * w + (uint64_t)__builtin_ctzll(x);
+            if (k < cap) oracle_encode(n, rho, &pairs[2 * k], &pairs[2 * k + 1]);
+            ++k;
+        }
+    return k;
+}
