@@ -1,6 +1,8 @@
-"""Write bitmap_digests.txt: SHA-256 and prime count of the oracle's dense
-prime bitmap for seeded functions too large for the oracle to run beside a
-GPU test (Algorithm 3, Section 4.1, in the oracle's bit-per-cube mode).
+"""Write bitmap_digests.txt: prime count and SHA-256 of the oracle's dense
+prime bitmap and of its (mask, value) list, for seeded functions too large
+for the oracle to run beside a GPU test (Algorithm 3, Section 4.1, in the
+oracle's bit-per-cube mode; the list in ascending rho as uint32 pairs, mask
+then value, little-endian).
 
 Calls only the oracle and the seeded input generator.  The packed state's
 words, read as bytes in little-endian order, are the dense LSB-first bitmap
@@ -38,7 +40,10 @@ def digest(n, seed, p_on, p_dc):
     A = (3 ** n + 7) // 8
     b = S.view(np.uint8)[:A]
     count = sum(int(POP[b[i: i + (1 << 26)]].sum(dtype=np.uint64)) for i in range(0, A, 1 << 26))
-    return hashlib.sha256(memoryview(b)).hexdigest(), count
+    h = hashlib.sha256(memoryview(b)).hexdigest()
+    pairs = oracle.packed_pairs(n, S)
+    assert len(pairs) == count
+    return h, count, hashlib.sha256(memoryview(np.ascontiguousarray(pairs, dtype="<u4"))).hexdigest()
 
 
 def main(ns):
@@ -50,15 +55,17 @@ def main(ns):
     for n in ns:
         n_, seed, p_on, p_dc = CASES[n]
         t0 = time.time()
-        h, count = digest(n_, seed, p_on, p_dc)
-        rows[n] = f"{n_} {seed} {p_on} {p_dc} {count} {h}"
-        print(f"n={n}: {count} primes, {h} ({time.time() - t0:.0f} s, {oracle.max_threads()} threads)", flush=True)
+        h, count, hl = digest(n_, seed, p_on, p_dc)
+        rows[n] = f"{n_} {seed} {p_on} {p_dc} {count} {h} {hl}"
+        print(f"n={n}: {count} primes, {h} {hl} ({time.time() - t0:.0f} s, {oracle.max_threads()} threads)",
+              flush=True)
     with open(OUT, "w") as f:
-        f.write("# SHA-256 and count of the dense prime bitmap (ceil(3^n/8) bytes, bit rho\n"
-                "# LSB-first) of seeded functions, from the oracle's bit-per-cube sweep\n"
+        f.write("# Prime count, SHA-256 of the dense prime bitmap (ceil(3^n/8) bytes, bit rho\n"
+                "# LSB-first) and SHA-256 of the (mask, value) list (uint32 pairs in ascending\n"
+                "# rho, little-endian) of seeded functions, from the oracle's bit-per-cube sweep\n"
                 "# (Algorithm 3, Section 4.1); written by make_digests.py in this folder.\n"
                 "# Function: synth.random_function(n, seed, p_on, p_dc); p_dc = 0 means no DC table.\n"
-                "# Columns: n seed p_on p_dc count sha256\n")
+                "# Columns: n seed p_on p_dc count bitmap_sha256 list_sha256\n")
         for n in sorted(rows):
             f.write(rows[n] + "\n")
 

@@ -375,6 +375,15 @@ def test_expected_prime_count_band():
 
 # ---------------------------------------------------------------- packed mode
 
+def test_packed_pairs_equal_byte_pairs():
+    """The packed mode's list equals the byte mode's (ascending rho, same encoding)."""
+    for n, seed, p, q in ((0, 1, 0.9, 0.0), (3, 1, 0.7, 0.0), (9, 2, 0.8, 0.05), (14, 1, 0.85, 0.0),
+                          (16, 3, 0.5, 0.2)):
+        on, dc = synth.random_function(n, seed, p, q)
+        want = oracle.pairs(n, oracle.sweep(n, on, dc))
+        assert np.array_equal(oracle.packed_pairs(n, oracle.sweep_packed(n, on, dc)), want), n
+
+
 def packed_cells(n, on, dc=None, threads=0):
     return bf.bool_from_bitmap(oracle.packed_bitmap(n, oracle.sweep_packed(n, on, dc, threads)), n)
 
@@ -431,11 +440,12 @@ def test_digest_script_matches_byte_oracle():
     import hashlib
     md = _make_digests()
     for n, seed, p, q in ((9, 2, 0.8, 0.05), (14, 1, 0.85, 0.0)):
-        h, c = md.digest(n, seed, p, q)
+        h, c, hl = md.digest(n, seed, p, q)
         on, dc = synth.random_function(n, seed, p, q)
         S = oracle.sweep(n, on, dc)
         assert h == hashlib.sha256(oracle.bitmap(n, S).tobytes()).hexdigest()
         assert c == oracle.count(n, S)
+        assert hl == hashlib.sha256(oracle.pairs(n, S).astype("<u4").tobytes()).hexdigest()
 
 
 def test_stored_digest_counts_near_expectation():
@@ -446,8 +456,8 @@ def test_stored_digest_counts_near_expectation():
         pytest.skip("no stored digests")
     rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
     assert rows
-    for n, seed, p_on, p_dc, count, h in rows:
+    for n, seed, p_on, p_dc, count, h, hl in rows:
         n, p_on, p_dc, count = int(n), float(p_on), float(p_dc), int(count)
-        assert len(h) == 64 and int(h, 16) >= 0
+        assert len(h) == len(hl) == 64 and int(h, 16) >= 0 and int(hl, 16) >= 0
         e = bf.expected_primes(n, p_on + (1 - p_on) * p_dc)
         assert abs(count - e) / e < 0.01, (n, count, e)

@@ -1,14 +1,16 @@
 """n = 23 and n = 24 (the benchmark workload) bit-exact, at sizes where the
 oracle cannot run beside the test: the SHA-256 of libdqmc.so's prime bitmap
-(through the C ABI) and its prime count against the oracle's.  The oracle's
-values are in tests/golden/bitmap_digests.txt, written by
-tests/golden/make_digests.py, which runs only the oracle (its bit-per-cube
-sweep, Algorithm 3, Section 4.1) and the seeded input generator.  Equal
-digests mean equal bitmaps, bit for bit.  In a module collected after the
-others: the n = 24 bitmap takes 35 GB of host memory."""
+and of its (mask, value) list (through the C ABI), and its prime count,
+against the oracle's.  The oracle's values are in
+tests/golden/bitmap_digests.txt, written by tests/golden/make_digests.py,
+which runs only the oracle (its bit-per-cube sweep, Algorithm 3, Section 4.1)
+and the seeded input generator.  Equal digests mean equal bitmaps and lists,
+bit for bit.  In a module collected after the others: the n = 24 bitmap takes
+35 GB of host memory."""
 import hashlib
 import os
 
+import numpy as np
 import pytest
 
 from paper_2302_10083_gb300 import dqmc, synth
@@ -25,8 +27,8 @@ def _cases():
     if os.path.exists(GOLDEN):
         for line in open(GOLDEN):
             if line.strip() and not line.startswith("#"):
-                n, seed, p_on, p_dc, count, h = line.split()
-                out[int(n)] = (int(seed), float(p_on), float(p_dc), int(count), h)
+                n, seed, p_on, p_dc, count, h, hl = line.split()
+                out[int(n)] = (int(seed), float(p_on), float(p_dc), int(count), h, hl)
     return out
 
 
@@ -69,10 +71,10 @@ def _gpu():
 
 
 @pytest.mark.parametrize("n", [23, 24])
-def test_bitmap_digest_and_count(n):
+def test_bitmap_list_digests_and_count(n):
     if n not in CASES:
         pytest.skip(f"no stored digest for n = {n}")
-    seed, p_on, p_dc, count, want = CASES[n]
+    seed, p_on, p_dc, count, want, want_list = CASES[n]
     A = (3 ** n + 7) // 8
     if _mem_available_bytes() < A + (4 << 30):
         pytest.skip(f"needs about {(A >> 30) + 4} GiB of available host memory")
@@ -86,3 +88,6 @@ def test_bitmap_digest_and_count(n):
     assert hashlib.sha256(memoryview(got)).hexdigest() == want
     del got
     assert dqmc.dqmc_count(n, on, dc) == count
+    pairs, c = dqmc.dqmc_list(n, on, dc, cap=count)
+    assert c == count and pairs.shape == (count, 2)
+    assert hashlib.sha256(memoryview(np.ascontiguousarray(pairs, dtype="<u4"))).hexdigest() == want_list
