@@ -1,9 +1,9 @@
-"""The bench's multi-rank logic on the host, as two gloo ranks (no GPU): every
-rank takes the largest step time over the ranks, and the whole-job value is
-the units all ranks processed over that time; the reference arm under a
-two-process launch prints one JSON line, from rank 0, and every rank exits 0.
-The sweep itself has no exchange step (one function per rank), so these are
-the only cross-rank paths."""
+"""The bench's host logic (no GPU).  As two gloo ranks: every rank takes the
+largest step time over the ranks, and the whole-job value is the units all
+ranks processed over that time; the reference arm under a two-process launch
+prints one JSON line, from rank 0, and every rank exits 0.  The sweep itself
+has no exchange step (one function per rank), so these are the only
+cross-rank paths.  Also the kernel count the batched line claims."""
 import json
 import os
 import socket
@@ -65,3 +65,21 @@ def test_reference_arm_two_ranks_prints_one_line():
     assert d["config"]["sample_n"] == 10
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "cubes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_launches_per_graph_counts_kernels():
+    """The batched line's kernel count: one launch per n on the shared-memory
+    path and for the one-tile kernel (n <= 12), one per pass for n = 13, 14 on
+    the streaming path.  With the built-in table the workload's n = 4..14 take
+    11 launches per graph (10 shared-memory classes and the one-tile n = 4)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2302_10083_gb300 import dqmc
+    table = dqmc.batch_tuning_table()
+    ns = list(range(4, 15)) * 3
+    assert bench.launches_per_graph(ns, table) == 11
+    tiles = dict(table)
+    for n in (13, 14):
+        tiles[str(n)] = dict(table[str(n)], path=dqmc.DQMC_BATCH_PATH_TILES)
+    assert bench.launches_per_graph(ns, tiles) == 9 + dqmc.dqmc_plan_passes(13) + dqmc.dqmc_plan_passes(14)
+    assert bench.launches_per_graph([4, 4, 7], table) == 2
