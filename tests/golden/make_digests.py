@@ -9,7 +9,7 @@ words, read as bytes in little-endian order, are the dense LSB-first bitmap
 (cube rho at bit rho % 8 of byte rho // 8; bits past 3^n stay 0), so the
 digest is taken over its first ceil(3^n / 8) bytes without a copy.
 
-    python tests/golden/make_digests.py [n ...]     (default: 23 24)
+    python tests/golden/make_digests.py [n ...]     (default: 22 23 24)
 """
 import hashlib
 import os
@@ -27,9 +27,9 @@ from paper_2302_10083_gb300 import synth  # noqa: E402
 
 OUT = os.path.join(HERE, "bitmap_digests.txt")
 
-# (n, seed, p_on, p_dc): n = 23 as the sampled n = 23 GPU case; n = 24 the
-# benchmark workload (ON ~ Bernoulli(0.85), seed 1, no don't-cares)
-CASES = {23: (23, 2, 0.8, 0.05), 24: (24, 1, 0.85, 0.0)}
+# (n, seed, p_on, p_dc): n = 22, 23 as the sampled GPU cases of those sizes;
+# n = 24 the benchmark workload (ON ~ Bernoulli(0.85), seed 1, no don't-cares)
+CASES = {22: (22, 2, 0.8, 0.05), 23: (23, 2, 0.8, 0.05), 24: (24, 1, 0.85, 0.0)}
 
 POP = np.array([bin(i).count("1") for i in range(256)], dtype=np.uint8)
 

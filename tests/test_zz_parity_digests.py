@@ -1,4 +1,4 @@
-"""n = 23 and n = 24 (the benchmark workload) bit-exact, at sizes where the
+"""n = 22, 23 and 24 (the benchmark workload) bit-exact, at sizes where the
 oracle cannot run beside the test: the SHA-256 of libdqmc.so's prime bitmap
 and of its (mask, value) list (through the C ABI), and its prime count,
 against the oracle's.  The oracle's values are in
@@ -70,7 +70,7 @@ def _gpu():
     dqmc.dqmc_release()
 
 
-@pytest.mark.parametrize("n", [23, 24])
+@pytest.mark.parametrize("n", [22, 23, 24])
 def test_bitmap_list_digests_and_count(n):
     if n not in CASES:
         pytest.skip(f"no stored digest for n = {n}")
