@@ -70,6 +70,9 @@ def test_bad_arguments_rejected_without_gpu():
     assert L.dqmc_list_dev(8, 256, None, 256, None, 0, None, 256, 1 << 20, None) == dqmc.DQMC_EINVAL
     assert L.dqmc_compact_dev(8, None, None, 0, 256, 256, 1 << 20, None) == dqmc.DQMC_EINVAL
     assert L.dqmc_plan_json(26, None, 0) == dqmc.DQMC_EINVAL
+    # the static-workspace sweep takes n <= 15 only: larger n is refused before any CUDA call
+    assert L.dqmc_primes_dev_static(16, 256, None, 256, None, None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_primes_dev_static(26, 256, None, 256, None, None) == dqmc.DQMC_EINVAL
 
 
 def test_batch_arguments_rejected_without_gpu():
