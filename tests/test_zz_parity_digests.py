@@ -5,8 +5,8 @@ against the oracle's.  The oracle's values are in
 tests/golden/bitmap_digests.txt, written by tests/golden/make_digests.py,
 which runs only the oracle (its bit-per-cube sweep, Algorithm 3, Section 4.1)
 and the seeded input generator.  Equal digests mean equal bitmaps and lists,
-bit for bit.  In a module collected after the others: the n = 24 bitmap takes
-35 GB of host memory."""
+bit for bit.  In a module collected after the other parity tests (the n = 24 bitmap
+takes 35 GB of host memory); only the static-workspace test follows it."""
 import hashlib
 import os
 

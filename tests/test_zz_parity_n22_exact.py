@@ -1,7 +1,7 @@
 """n = 22 bit-exact: the prime bitmap and count of libdqmc.so (through its C
 ABI) against the oracle's bit-per-cube mode (3.9 GB; the byte-per-cube state
 would be 31 GB).  The same function as the sampled n = 22 case.  In a module
-of its own, collected after the others: it holds about 12 GB of host memory
+of its own, collected near the end: it holds about 12 GB of host memory
 and runs the oracle for a minute or two."""
 import numpy as np
 import pytest
