@@ -524,3 +524,15 @@ def test_plan_json_fields_as_documented(n):
         if q["kind"] == "super":
             assert q["window"] == q["step_size"] == q["n_sb"] and q["n_steps"] == q["groups"] == 1
     assert (p["state_rows"] == 0) == (p["passes"][0]["kind"] == "whole")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: with the library absent (and no build allowed), the
+    binding raises instead of computing anything."""
+    monkeypatch.setattr(dqmc, "_lib", None)
+    monkeypatch.setattr(dqmc._build, "LIB", str(tmp_path / "libdqmc.so"))
+    with pytest.raises(RuntimeError, match="libdqmc.so not found"):
+        dqmc.lib(build_if_missing=False)
+    monkeypatch.setattr(dqmc._build, "up_to_date", lambda: True)
+    with pytest.raises(RuntimeError, match="libdqmc.so not found"):
+        dqmc.dqmc_primes(4, np.zeros(2, dtype=np.uint8))
