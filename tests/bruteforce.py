@@ -123,6 +123,29 @@ def symmetric_prime_count(n: int, W) -> int:
 
 # ---- expectations for i.i.d. Bernoulli(p) support ---------------------------
 
+def rho_positive(n: int, m: int) -> int:
+    """rho of the positive term of point m: digit i is 1 where m has x_i, else *."""
+    return sum((1 if (m >> i) & 1 else 2) * 3 ** i for i in range(n))
+
+
+def monotone_case(n: int, seed: int):
+    """A monotone function with no symmetry (an OR of 3n random positive
+    terms) as a support array, and its minimal true points in ascending rho
+    of their positive terms."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(1 << n)
+    sup = np.zeros(1 << n, dtype=bool)
+    for _ in range(3 * n):
+        size = int(rng.integers(1, max(2, n // 2) + 1))
+        T = int(np.bitwise_or.reduce(1 << rng.choice(n, size=size, replace=False)))
+        sup |= (t & T) == T
+    minimal = sup.copy()
+    for i in range(n):
+        has = ((t >> i) & 1) == 1
+        minimal &= ~(has & sup[t ^ (1 << i)])
+    return sup, sorted(t[minimal].tolist(), key=lambda m: rho_positive(n, m))
+
+
 def expected_implicants(n: int, p: float) -> float:
     return sum(comb(n, w) * 2 ** (n - w) * p ** (2 ** w) for w in range(n + 1))
 

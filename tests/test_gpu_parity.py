@@ -145,6 +145,22 @@ def test_symmetric(n, W):
         assert np.array_equal(got, bf.symmetric_prime_cells(n, W))
 
 
+@pytest.mark.parametrize("n,seed", [(12, 4), (13, 5), (16, 7), (20, 8)])
+def test_monotone(n, seed):
+    """Monotone functions with no symmetry: the primes are the positive terms
+    of the minimal true points (closed form, Section 2's definitions), across
+    the one-tile kernel (n = 12) and the pass kernels (n >= 13)."""
+    sup, mins = bf.monotone_case(n, seed)
+    on = bf.bitmap_from_bool(sup)
+    pairs, cnt = dqmc.dqmc_list(n, on, None, cap=len(mins) + 8)
+    assert cnt == len(mins)
+    assert pairs.tolist() == [[m, m] for m in mins]
+    want = np.zeros((3 ** n + 7) // 8, dtype=np.uint8)
+    for r in (bf.rho_positive(n, m) for m in mins):
+        want[r >> 3] |= np.uint8(1 << (r & 7))
+    assert np.array_equal(dqmc.dqmc_primes(n, on), want)
+
+
 def test_list_truncation():
     n = 11
     on, _ = synth.random_function(n, 4, 0.6)

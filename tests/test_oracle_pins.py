@@ -223,27 +223,6 @@ def test_symmetric_closed_form(n, W):
     assert oracle.count(n, S) == bf.symmetric_prime_count(n, W)
 
 
-def _rho_positive(n, m):
-    """rho of the positive term of point m: digit i is 1 where m has x_i, else *."""
-    return sum((1 if (m >> i) & 1 else 2) * 3 ** i for i in range(n))
-
-
-def _monotone_case(n, seed):
-    """An OR of random positive terms (no symmetry) and its minimal true points."""
-    rng = np.random.default_rng(seed)
-    t = np.arange(1 << n)
-    sup = np.zeros(1 << n, dtype=bool)
-    for _ in range(3 * n):
-        size = int(rng.integers(1, max(2, n // 2) + 1))
-        T = int(np.bitwise_or.reduce(1 << rng.choice(n, size=size, replace=False)))
-        sup |= (t & T) == T
-    minimal = sup.copy()
-    for i in range(n):
-        has = ((t >> i) & 1) == 1
-        minimal &= ~(has & sup[t ^ (1 << i)])
-    return sup, sorted(t[minimal].tolist(), key=lambda m: _rho_positive(n, m))
-
-
 @pytest.mark.parametrize("n,seed", [(5, 1), (8, 2), (10, 3), (12, 4)])
 def test_monotone_closed_form(n, seed):
     """A monotone (positive) function's primes are exactly the positive terms
@@ -251,9 +230,9 @@ def test_monotone_closed_form(n, seed):
     positive term would be true below a minimal point, and a literal x_i' can
     be dropped from any implicant since raising x_i keeps f true).  The list
     is pinned too: minimal point m gives the pair (m, m)."""
-    sup, mins = _monotone_case(n, seed)
+    sup, mins = bf.monotone_case(n, seed)
     S = oracle.sweep(n, bf.bitmap_from_bool(sup))
-    assert np.nonzero(S)[0].tolist() == [_rho_positive(n, m) for m in mins]
+    assert np.nonzero(S)[0].tolist() == [bf.rho_positive(n, m) for m in mins]
     assert oracle.pairs(n, S).tolist() == [[m, m] for m in mins]
 
 
@@ -445,9 +424,9 @@ def test_packed_symmetric_closed_form(n, W):
 def test_packed_monotone_closed_form(n, seed):
     """The monotone closed form (primes = positive terms of the minimal true
     points) in the bit-per-cube mode."""
-    sup, mins = _monotone_case(n, seed)
+    sup, mins = bf.monotone_case(n, seed)
     want = np.zeros(3 ** n, dtype=bool)
-    want[[_rho_positive(n, m) for m in mins]] = True
+    want[[bf.rho_positive(n, m) for m in mins]] = True
     assert np.array_equal(packed_cells(n, bf.bitmap_from_bool(sup)), want)
 
 
