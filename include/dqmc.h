@@ -121,14 +121,17 @@ void dqmc_release(void);
  * least dqmc_workspace_bytes(n) bytes, 256-byte aligned, and must not be used
  * by another call that overlaps on the device.  Inputs are read-only. */
 
-/* d_on, d_dc: ceil(2^n/8)-byte truth tables (d_dc may be NULL).
+/* The prime bitmap, as dqmc_primes (Algorithm 3 of Section 4.1: MergeAll,
+ * then ReduceAll; the set cells are Section 2's prime implicants).
+ * d_on, d_dc: ceil(2^n/8)-byte truth tables (d_dc may be NULL).
  * d_bitmap: dqmc_bitmap_alloc_bytes(n) bytes, receives the prime bitmap.
  * d_count: one uint64, receives the number of primes (may be NULL). */
 int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc,
                     void *d_bitmap, uint64_t *d_count,
                     void *d_work, uint64_t work_bytes, void *stream);
 
-/* Same sweep, then compaction of the bitmap into (mask, value) pairs.
+/* Same sweep, then compaction of the bitmap into (mask, value) pairs in
+ * ascending rho (the output extraction step of Algorithm 4, Section 4.2).
  * d_pairs: 2*cap uint32 (may be NULL when cap = 0).  d_count: one uint64,
  * receives the number of primes (required).  Pairs at index >= cap are not
  * written; the caller compares *d_count with cap after the stream completes. */
@@ -163,7 +166,8 @@ int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *s
 int dqmc_primes_dev_static(uint32_t n, const void *d_on, const void *d_dc,
                            void *d_bitmap, uint64_t *d_count, void *stream);
 
-/* Compaction alone: (mask, value) pairs of the set bits of an existing dense
+/* Compaction alone (the output extraction step of Algorithm 4, Section 4.2):
+ * (mask, value) pairs, in ascending rho, of the set bits of an existing dense
  * bitmap of an n-variable function.  d_work as above (only its scan part is
  * used).  d_count: one uint64 (required). */
 int dqmc_compact_dev(uint32_t n, const void *d_bitmap, uint32_t *d_pairs,
