@@ -146,6 +146,23 @@ def monotone_case(n: int, seed: int):
     return sup, sorted(t[minimal].tolist(), key=lambda m: rho_positive(n, m))
 
 
+def rho_of_pair(n: int, mask: int, value: int) -> int:
+    """rho of the cube whose (mask, value) pair is given: digit i is * where
+    mask has no bit i, else value's bit i."""
+    return sum(((value >> i) & 1 if (mask >> i) & 1 else 2) * 3 ** i for i in range(n))
+
+
+def unate_case(n: int, seed: int, nu: int):
+    """The monotone function of monotone_case with the inputs in nu negated,
+    g(x) = f(x xor nu), as a support array, and its primes in closed form as
+    (mask, value) pairs in ascending rho: minimal true point m of f gives the
+    cube with literal x_i = 1 xor nu_i for i in m, * elsewhere."""
+    sup, mins = monotone_case(n, seed)
+    t = np.arange(1 << n)
+    pairs = sorted(((m, m & ~nu & ((1 << n) - 1)) for m in mins), key=lambda p: rho_of_pair(n, *p))
+    return sup[t ^ nu], pairs
+
+
 def expected_implicants(n: int, p: float) -> float:
     return sum(comb(n, w) * 2 ** (n - w) * p ** (2 ** w) for w in range(n + 1))
 

@@ -161,6 +161,17 @@ def test_monotone(n, seed):
     assert np.array_equal(dqmc.dqmc_primes(n, on), want)
 
 
+@pytest.mark.parametrize("n,seed,nu", [(11, 13, 0b01010101010), (14, 14, 0b10110011100101),
+                                       (17, 15, 0b01101001011010011)])
+def test_unate(n, seed, nu):
+    """Unate functions (monotone with the inputs in nu negated): primes with
+    both 0 and 1 literals, in closed form."""
+    sup, want = bf.unate_case(n, seed, nu)
+    pairs, cnt = dqmc.dqmc_list(n, bf.bitmap_from_bool(sup), None, cap=len(want) + 8)
+    assert cnt == len(want)
+    assert pairs.tolist() == [[m, v] for m, v in want]
+
+
 def test_list_truncation():
     n = 11
     on, _ = synth.random_function(n, 4, 0.6)

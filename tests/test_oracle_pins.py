@@ -236,6 +236,22 @@ def test_monotone_closed_form(n, seed):
     assert oracle.pairs(n, S).tolist() == [[m, m] for m in mins]
 
 
+@pytest.mark.parametrize("n,seed,nu", [(6, 11, 0b101101), (9, 12, 0b110010011), (11, 13, 0b01010101010)])
+def test_unate_closed_form(n, seed, nu):
+    """A unate function (a monotone function with the inputs in nu negated)
+    has the monotone closed form with the literals' polarity flipped where nu
+    is set, so its primes mix 0 and 1 digits: pinned cell by cell and in the
+    list, byte and bit-per-cube modes."""
+    sup, want = bf.unate_case(n, seed, nu)
+    on = bf.bitmap_from_bool(sup)
+    S = oracle.sweep(n, on)
+    assert np.nonzero(S)[0].tolist() == [bf.rho_of_pair(n, m, v) for m, v in want]
+    assert oracle.pairs(n, S).tolist() == [[m, v] for m, v in want]
+    cells = np.zeros(3 ** n, dtype=bool)
+    cells[[bf.rho_of_pair(n, m, v) for m, v in want]] = True
+    assert np.array_equal(packed_cells(n, on), cells)
+
+
 def test_majority_count():
     """Odd-n majority has C(n, (n+1)/2) primes."""
     from math import comb
