@@ -129,3 +129,20 @@ def test_unmutated_packed_copy_passes(tmp_path):
 @pytest.mark.parametrize("name", sorted(PACKED_MUTANTS))
 def test_packed_mutant_is_caught(tmp_path, name):
     assert not pins_pass(build_mutant(tmp_path, name)), name
+
+
+def unate_pin_passes(sweep):
+    """The unate closed form alone (no don't-cares, no brute force)."""
+    for n, seed, nu in ((6, 11, 0b101101), (9, 12, 0b110010011), (11, 13, 0b01010101010)):
+        sup, want = bf.unate_case(n, seed, nu)
+        got = np.nonzero(sweep(n, bf.bitmap_from_bool(sup)))[0].tolist()
+        if got != [bf.rho_of_pair(n, m, v) for m, v in want]:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(set(MUTANTS) - {"ignore_dc"} | set(PACKED_MUTANTS)))
+def test_unate_pin_alone_catches(tmp_path, name):
+    """An independent second net: the unate closed form catches every planted
+    mistake that can show without don't-cares."""
+    assert not unate_pin_passes(build_mutant(tmp_path, name)), name
