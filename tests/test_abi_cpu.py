@@ -536,3 +536,23 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dqmc._build, "up_to_date", lambda: True)
     with pytest.raises(RuntimeError, match="libdqmc.so not found"):
         dqmc.dqmc_primes(4, np.zeros(2, dtype=np.uint8))
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    """The oracle and the CUDA path are independent: no file of the package or
+    of include/ names the oracle, and no oracle file names the package, its
+    headers or its sources.  Only the seeded input generator (synth.py, no
+    method arithmetic) is used by both, and by the tests alone on the oracle
+    side."""
+    pkg = os.path.join(ROOT, "paper_2302_10083_gb300")
+    product = [p for ext in ("py", "cu", "cuh", "h") for p in glob.glob(os.path.join(pkg, "**", "*." + ext),
+                                                                         recursive=True)]
+    product += glob.glob(os.path.join(ROOT, "include", "*.h"))
+    for p in product:
+        text = open(p).read()
+        if p.endswith("synth.py"):
+            text = text.split('"""', 2)[-1]   # its docstring names the oracle as a user
+        assert not re.search(r"\boracle\b|dqmc_oracle", text), p
+    for p in glob.glob(os.path.join(ROOT, "oracle", "*.py")) + glob.glob(os.path.join(ROOT, "oracle", "*.c")):
+        text = open(p).read()
+        assert not re.search(r"paper_2302_10083_gb300|libdqmc\.so|dqmc\.h|csrc|#include \"", text), p
