@@ -132,17 +132,32 @@ def test_packed_mutant_is_caught(tmp_path, name):
 
 
 def unate_pin_passes(sweep):
-    """The unate closed form alone (no don't-cares, no brute force)."""
+    """The unate closed forms alone (no brute force): the function itself, and
+    its minimal true points as ON with the other true points as don't-cares."""
     for n, seed, nu in ((6, 11, 0b101101), (9, 12, 0b110010011), (11, 13, 0b01010101010)):
         sup, want = bf.unate_case(n, seed, nu)
-        got = np.nonzero(sweep(n, bf.bitmap_from_bool(sup)))[0].tolist()
-        if got != [bf.rho_of_pair(n, m, v) for m, v in want]:
+        rho = [bf.rho_of_pair(n, m, v) for m, v in want]
+        if np.nonzero(sweep(n, bf.bitmap_from_bool(sup)))[0].tolist() != rho:
+            return False
+        on = np.zeros(1 << n, dtype=bool)
+        on[[m ^ nu for m, _ in want]] = True
+        got = sweep(n, bf.bitmap_from_bool(on), bf.bitmap_from_bool(sup & ~on))
+        if np.nonzero(got)[0].tolist() != rho:
             return False
     return True
 
 
-@pytest.mark.parametrize("name", sorted(set(MUTANTS) - {"ignore_dc"} | set(PACKED_MUTANTS)))
+def test_unate_pin_passes_unmutated(tmp_path):
+    old = MUTANTS["ignore_dc"][0]
+    MUTANTS["_identity"] = (old, old)
+    try:
+        assert unate_pin_passes(build_mutant(tmp_path, "_identity"))
+    finally:
+        del MUTANTS["_identity"]
+
+
+@pytest.mark.parametrize("name", sorted(set(MUTANTS) | set(PACKED_MUTANTS)))
 def test_unate_pin_alone_catches(tmp_path, name):
-    """An independent second net: the unate closed form catches every planted
-    mistake that can show without don't-cares."""
+    """An independent second net: the unate closed forms (with and without
+    don't-cares) catch every planted mistake on their own."""
     assert not unate_pin_passes(build_mutant(tmp_path, name)), name

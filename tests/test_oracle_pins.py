@@ -252,6 +252,23 @@ def test_unate_closed_form(n, seed, nu):
     assert np.array_equal(packed_cells(n, on), cells)
 
 
+@pytest.mark.parametrize("n,seed,nu", [(6, 11, 0b101101), (10, 16, 0b1001110001)])
+def test_unate_dont_care_closed_form(n, seed, nu):
+    """Don't-cares in closed form: ON = the unate function's minimal true
+    points alone, DC = the rest of its true points.  The implicants are those
+    of ON u DC (the don't-care reading of the scope), so the primes are the
+    unate closed form again; without the don't-cares they would be the ON
+    minterms themselves (an antichain has no two adjacent points)."""
+    sup, want = bf.unate_case(n, seed, nu)
+    on = np.zeros(1 << n, dtype=bool)
+    on[[m ^ nu for m, _ in want]] = True
+    dc = sup & ~on
+    S = oracle.sweep(n, bf.bitmap_from_bool(on), bf.bitmap_from_bool(dc))
+    assert oracle.pairs(n, S).tolist() == [[m, v] for m, v in want]
+    S0 = oracle.sweep(n, bf.bitmap_from_bool(on))
+    assert oracle.count(n, S0) == len(want) and np.array_equal(oracle.pairs(n, S0)[:, 0], np.full(len(want), (1 << n) - 1))
+
+
 def test_majority_count():
     """Odd-n majority has C(n, (n+1)/2) primes."""
     from math import comb
