@@ -197,7 +197,6 @@ def cpu_baseline(n=CPU_BASELINE_N):
     t1 = time.perf_counter()
     oracle.sweep(n1, on1, threads=1)
     dt1 = time.perf_counter() - t1
-    oracle.sweep(0, bytes([1]), threads=cores)   # the thread count persists: put it back
     return {"value": 3 ** n / dt, "unit": "cubes/s", "cores": cores, "kind": "oracle",
             "sample": f"one n={n} function of the same family (ON ~ Bernoulli({P_ON}), seed 1): full oracle "
                       f"sweep (Algorithm 3, one byte per cube, OpenMP), {dt:.2f} s; cubes/s = 3^{n}/time",

@@ -68,12 +68,26 @@ static uint64_t rho_of_minterm(int n, uint64_t t)
     return r;
 }
 
-static void set_threads(int threads)
+/* threads > 0 sets the thread count for one call; the previous count is
+ * returned and put back by restore_threads when the call ends. */
+static int set_threads(int threads)
 {
 #ifdef _OPENMP
+    const int prev = omp_get_max_threads();
     if (threads > 0) omp_set_num_threads(threads);
+    return prev;
 #else
     (void)threads;
+    return 1;
+#endif
+}
+
+static void restore_threads(int prev)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(prev);
+#else
+    (void)prev;
 #endif
 }
 
@@ -95,7 +109,7 @@ void oracle_sweep(int n, const uint8_t *on, const uint8_t *dc, uint8_t *S,
 {
     const uint64_t N = oracle_pow3(n);
     const uint64_t T = (uint64_t)1 << n;
-    set_threads(threads);
+    const int prev_threads = set_threads(threads);
 
     /* Load the input: S = indicator of the support embedded in {0,1,*}^n. */
     memset(S, 0, N);
@@ -143,6 +157,7 @@ void oracle_sweep(int n, const uint8_t *on, const uint8_t *dc, uint8_t *S,
         counts[0] = merges;
         counts[1] = reduces;
     }
+    restore_threads(prev_threads);
 }
 
 /* Dense LSB-first bitmap of the byte state: bit rho set iff S[rho] != 0. */
@@ -238,10 +253,11 @@ int oracle_is_prime(int n, const uint8_t *on, const uint8_t *dc, uint64_t rho)
 void oracle_is_prime_many(int n, const uint8_t *on, const uint8_t *dc,
                           const uint64_t *rhos, uint64_t count, uint8_t *out, int threads)
 {
-    set_threads(threads);
+    const int prev_threads = set_threads(threads);
     #pragma omp parallel for schedule(dynamic, 64)
     for (uint64_t k = 0; k < count; ++k)
         out[k] = (uint8_t)oracle_is_prime(n, on, dc, rhos[k]);
+    restore_threads(prev_threads);
 }
 
 /*
@@ -275,7 +291,7 @@ void oracle_sweep_packed(int n, const uint8_t *on, const uint8_t *dc, uint64_t *
     const uint64_t N = oracle_pow3(n);
     const uint64_t W = (N + 63) / 64;
     const uint64_t T = (uint64_t)1 << n;
-    set_threads(threads);
+    const int prev_threads = set_threads(threads);
 
     /* Load the input: bit rho(t) = I(t) for every minterm t. */
     memset(S, 0, W * sizeof(uint64_t));
@@ -332,6 +348,7 @@ void oracle_sweep_packed(int n, const uint8_t *on, const uint8_t *dc, uint64_t *
         }
         d *= 3u;
     }
+    restore_threads(prev_threads);
 }
 
 /* The packed state as the dense LSB-first bitmap: byte k holds cubes 8k..8k+7. */

@@ -362,7 +362,9 @@ def test_triple_counts(n):
 
 def test_threads_agree():
     on, dc = synth.random_function(14, 9, 0.8, 0.1)
+    cores = oracle.max_threads()
     a = oracle.sweep(14, on, dc, threads=1)
+    assert oracle.max_threads() == cores   # the thread count applies to that call only
     b = oracle.sweep(14, on, dc, threads=0)
     assert np.array_equal(a, b)
 
