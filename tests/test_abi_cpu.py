@@ -556,3 +556,11 @@ def test_oracle_and_cuda_path_share_no_code():
     for p in glob.glob(os.path.join(ROOT, "oracle", "*.py")) + glob.glob(os.path.join(ROOT, "oracle", "*.c")):
         text = open(p).read()
         assert not re.search(r"paper_2302_10083_gb300|libdqmc\.so|dqmc\.h|csrc|#include \"", text), p
+
+
+def test_static_workspace_tests_collected_last():
+    """The static-workspace GPU test sits in the module pytest collects last
+    (files in name order), so a run that stops at its first failure has run
+    every other test before it."""
+    files = sorted(os.path.basename(p) for p in glob.glob(os.path.join(ROOT, "tests", "test_*.py")))
+    assert files[-1] == "test_zzz_no_alloc.py", files[-3:]
