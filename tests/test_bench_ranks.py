@@ -83,3 +83,17 @@ def test_launches_per_graph_counts_kernels():
         tiles[str(n)] = dict(table[str(n)], path=dqmc.DQMC_BATCH_PATH_TILES)
     assert bench.launches_per_graph(ns, tiles) == 9 + dqmc.dqmc_plan_passes(13) + dqmc.dqmc_plan_passes(14)
     assert bench.launches_per_graph([4, 4, 7], table) == 2
+
+
+def test_cpu_baseline_fields():
+    """The bench's cpu_baseline: the oracle on every host thread, and the same
+    oracle on one thread beside it, without changing the thread count later
+    calls get."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    cores = oracle.max_threads()
+    d = bench.cpu_baseline(12)
+    assert d["kind"] == "oracle" and d["unit"] == "cubes/s" and d["value"] > 0 and d["cores"] == cores
+    assert d["one_core"]["cores"] == 1 and d["one_core"]["value"] > 0 and "n=9" in d["one_core"]["sample"]
+    assert oracle.max_threads() == cores
