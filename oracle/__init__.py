@@ -22,7 +22,8 @@ use and wraps it with ctypes:
 Pins (tests/test_oracle_pins.py): brute force for n <= 10 and every function of
 n <= 3 (n = 4 on request), the 3-bit majority (Section 1), the Merge example
 (Section 3), constant 0 and 1, parity, single minterm, OR of all variables,
-symmetric and monotone functions in closed form, invariants, metamorphic relations, the
+symmetric, monotone and unate functions in closed form (unate also with
+don't-cares), invariants, metamorphic relations, the
 triple counts of the Boolean-circuit theorem (Section 4.1).
 """
 from __future__ import annotations
