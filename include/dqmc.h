@@ -161,10 +161,20 @@ int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *s
  * share the array and it keeps the last call's contents (each sweep clears
  * what must start at zero); calls that overlap on the GPU, on any stream or
  * thread, race on it and must be serialised by the caller.  d_on, d_dc,
- * d_bitmap, d_count and stream as for dqmc_primes_dev.  The paper has no
- * counterpart: this is a deployment convenience. */
+ * d_bitmap, d_count and stream as for dqmc_primes_dev.  The array's device
+ * address is cached per device for the life of the process, so resetting a
+ * device (cudaDeviceReset) after the first call on it is not supported.  The
+ * paper has no counterpart: this is a deployment convenience. */
 int dqmc_primes_dev_static(uint32_t n, const void *d_on, const void *d_dc,
                            void *d_bitmap, uint64_t *d_count, void *stream);
+
+/* dqmc_dev_status for the static workspace of the current device: synchronises
+ * `stream`, then reports how the last dqmc_primes_dev_static sweep on this
+ * device ended (DQMC_OK, DQMC_ETIMEOUT or DQMC_ECUDA as for dqmc_dev_status;
+ * the error word lives in the static array, which the caller cannot address).
+ * n as given to that sweep (n > 15: DQMC_EINVAL).  Allocates nothing.  The
+ * paper has no counterpart. */
+int dqmc_dev_status_static(uint32_t n, void *stream);
 
 /* Compaction alone (the output extraction step of Algorithm 4, Section 4.2):
  * (mask, value) pairs, in ascending rho, of the set bits of an existing dense

@@ -27,33 +27,51 @@ static void *g_static_ptr[64];
 
 using namespace dqmc;
 
-extern "C" int dqmc_primes_dev_static(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
-                                      uint64_t *d_count, void *stream)
+// The array's device address on the current device (looked up once per device,
+// with that device current, and cached for the life of the process), or a
+// negative status.
+static int static_scratch(void **out)
 {
-    if (n > kStaticMaxN) return DQMC_EINVAL;
-    if (workspace_layout((int)n).total > kStaticScratchBytes) return DQMC_EINVAL;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
         return e == cudaSuccess ? DQMC_EINVAL : DQMC_ECUDA;
     }
-    void *ptr = nullptr;
-    {
-        // Set-up, once per device, with that device current: the device
-        // address of the array (its name in host code is only a host-side
-        // stand-in, not a device pointer).
-        std::lock_guard<std::mutex> g(g_static_mu);
-        if (!g_static_ptr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_static_scratch);
-            if (e != cudaSuccess || !p) {
-                cudaGetLastError();
-                return DQMC_ECUDA;
-            }
-            g_static_ptr[dev] = p;
+    // Set-up: the name of the array in host code is only a host-side
+    // stand-in, not a device pointer.
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DQMC_ECUDA;
         }
-        ptr = g_static_ptr[dev];
+        g_static_ptr[dev] = p;
     }
+    *out = g_static_ptr[dev];
+    return DQMC_OK;
+}
+
+extern "C" int dqmc_primes_dev_static(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
+                                      uint64_t *d_count, void *stream)
+{
+    if (n > kStaticMaxN) return DQMC_EINVAL;
+    if (workspace_layout((int)n).total > kStaticScratchBytes) return DQMC_EINVAL;
+    void *ptr = nullptr;
+    const int st = static_scratch(&ptr);
+    if (st != DQMC_OK) return st;
     return dqmc_primes_dev(n, d_on, d_dc, d_bitmap, d_count, ptr, kStaticScratchBytes, stream);
+}
+
+// How the last static-workspace sweep on this device ended: the error word
+// sits in the static array, whose address only the library knows.
+extern "C" int dqmc_dev_status_static(uint32_t n, void *stream)
+{
+    if (n > kStaticMaxN) return DQMC_EINVAL;
+    void *ptr = nullptr;
+    const int st = static_scratch(&ptr);
+    if (st != DQMC_OK) return st;
+    return dqmc_dev_status(n, ptr, kStaticScratchBytes, stream);
 }

@@ -66,6 +66,7 @@ _SIGS = {
                                              ctypes.c_uint64, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, c_vp, ctypes.c_uint64, ctypes.c_uint64, c_vp]),
     "dqmc_primes_dev_static": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "dqmc_dev_status_static": (ctypes.c_int, [ctypes.c_uint32, c_vp]),
     "dqmc_batch_run": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p, c_vp]),
     "dqmc_batch_workspace_bytes": (ctypes.c_uint64, [ctypes.c_uint32, c_u32p]),
     "dqmc_batch_release": (ctypes.c_int, []),
@@ -186,16 +187,38 @@ def dqmc_count(n: int, on_bits, dc_bits=None) -> int:
     return int(c.value)
 
 
+def _list_cap_guess(n: int, on, dc) -> int:
+    """A first list size for dqmc_list(cap=None): the expected prime count of a
+    function whose support has the same density with independent minterms,
+    with headroom.  Only sizes a host buffer; a function with more primes is
+    swept a second time with the exact count."""
+    from math import comb
+    m = 1 << n
+    sup = np.unpackbits(on[: (m + 7) >> 3], bitorder="little")[:m]
+    if dc is not None:
+        sup = sup | np.unpackbits(dc[: (m + 7) >> 3], bitorder="little")[:m]
+    p = float(sup.mean()) if m else 0.0
+    e = sum(comb(n, w) * 2.0 ** (n - w) * p ** (2 ** w) * (1.0 - p ** (2 ** w)) ** (n - w) for w in range(n + 1))
+    return int(1.1 * e) + 4096
+
+
 def dqmc_list(n: int, on_bits, dc_bits=None, cap: int | None = None):
-    """(pairs (count, 2) uint32, count).  With cap=None the list is sized by a count call."""
+    """(pairs (count, 2) uint32, count).  With cap=None the buffer is first
+    sized by the expected count of a random function of the same density; if
+    the true count is larger, the list is taken again at that size."""
     on = _host_tt(on_bits, n)
     dc = _host_tt(dc_bits, n)
-    if cap is None:
-        cap = dqmc_count(n, on, dc)
-    out = np.empty(2 * max(cap, 1), dtype=np.uint32)
-    c = ctypes.c_uint64()
-    st = lib().dqmc_list(n, _p8(on), _p8(dc), out.ctypes.data_as(c_u32p), cap, ctypes.byref(c))
-    _check(st, "dqmc_list", ok=(DQMC_OK, DQMC_ETRUNC))
+    auto = cap is None
+    if auto:
+        cap = _list_cap_guess(n, on, dc)
+    while True:
+        out = np.empty(2 * max(cap, 1), dtype=np.uint32)
+        c = ctypes.c_uint64()
+        st = lib().dqmc_list(n, _p8(on), _p8(dc), out.ctypes.data_as(c_u32p), cap, ctypes.byref(c))
+        _check(st, "dqmc_list", ok=(DQMC_OK, DQMC_ETRUNC))
+        if not (auto and st == DQMC_ETRUNC):
+            break
+        cap = int(c.value)
     k = min(int(c.value), cap)
     return out[: 2 * k].reshape(k, 2), int(c.value)
 
@@ -238,6 +261,11 @@ def dqmc_primes_dev_static(n, d_on, d_dc, d_bitmap, d_count, stream) -> int:
     """dqmc_primes_dev with the library's static 2 MiB workspace (n <= 15, allocates nothing)."""
     return _check(lib().dqmc_primes_dev_static(n, d_on, d_dc or None, d_bitmap, d_count or None, stream or None),
                   "dqmc_primes_dev_static")
+
+
+def dqmc_dev_status_static(n, stream) -> int:
+    """How the last dqmc_primes_dev_static sweep on the current device ended."""
+    return _check(lib().dqmc_dev_status_static(n, stream or None), "dqmc_dev_status_static")
 
 
 def dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream) -> int:

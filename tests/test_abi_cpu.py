@@ -73,6 +73,7 @@ def test_bad_arguments_rejected_without_gpu():
     # the static-workspace sweep takes n <= 15 only: larger n is refused before any CUDA call
     assert L.dqmc_primes_dev_static(16, 256, None, 256, None, None) == dqmc.DQMC_EINVAL
     assert L.dqmc_primes_dev_static(26, 256, None, 256, None, None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_dev_status_static(16, None) == dqmc.DQMC_EINVAL
 
 
 def test_batch_arguments_rejected_without_gpu():

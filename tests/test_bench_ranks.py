@@ -63,6 +63,10 @@ def test_reference_arm_two_ranks_prints_one_line():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 2 and d["warmup"] == 1
     assert d["unit"] == "cubes/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["config"]["sample_n"] == 10
+    # the same metric string as the main arm's line, so the two can be divided
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.single_metric(bench.N_MAIN)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "cubes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 

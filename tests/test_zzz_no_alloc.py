@@ -32,6 +32,9 @@ def _run_both(n, on, dc):
                                            buf.dc.data_ptr() if dc is not None else None,
                                            bm2.data_ptr(), c2.data_ptr(), sh)
     assert st == dqmc.DQMC_OK, dqmc.strerror(st)
+    # the static sweep's bounded waits and bounds checks report through the
+    # error word in the static array
+    assert dqmc.lib().dqmc_dev_status_static(n, sh) == dqmc.DQMC_OK
     buf.primes()
     torch.cuda.synchronize()
     return (buf.bitmap.cpu().numpy(), int(buf.count.item())), (bm2.cpu().numpy(), int(c2.item()))
@@ -53,3 +56,4 @@ def test_static_workspace_rejects_large_n():
     """n = 16 does not fit the 2 MiB array: rejected before any device work."""
     st = dqmc.lib().dqmc_primes_dev_static(16, ctypes.c_void_p(256), None, ctypes.c_void_p(256), None, None)
     assert st == dqmc.DQMC_EINVAL
+    assert dqmc.lib().dqmc_dev_status_static(16, None) == dqmc.DQMC_EINVAL
