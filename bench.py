@@ -60,10 +60,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--p-on", type=float, default=P_ON,
+                    help="single workload: ON density (the workload's is 0.85; 1.0 = constant 1)")
     ap.add_argument("--ref-n", type=int, default=REF_SAMPLE_N,
                     help="--impl reference: the n of the function the oracle sweeps per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="single workload: leave out the compact batched and serving results of the line")
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
     ap.add_argument("--serve-jobs", type=int, default=2000, help="serving: jobs per arrival rate at most")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving: arrival span per rate at most")
@@ -259,11 +263,12 @@ def run_ours(args, rank, world, local):
 
     n = args.n
     seed = 1 + rank
-    on, _ = synth.random_function(n, seed, P_ON)
+    p_on = args.p_on
+    on, _ = synth.random_function(n, seed, p_on)
     L = dqmc.lib()
     # expected primes + 5% headroom sizes the list buffer
     from math import comb
-    exp_primes = sum(comb(n, w) * 2 ** (n - w) * P_ON ** (2 ** w) * (1 - P_ON ** (2 ** w)) ** (n - w)
+    exp_primes = sum(comb(n, w) * 2 ** (n - w) * p_on ** (2 ** w) * (1 - p_on ** (2 ** w)) ** (n - w)
                      for w in range(n + 1))
     cap = int(exp_primes * 1.05) + 1024
     buf = dqmc.DeviceBuffers(n, device=f"cuda:{local}", with_dc=False, cap=cap)
@@ -339,7 +344,7 @@ def run_ours(args, rank, world, local):
         "value": value, "unit": "cubes/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 bitwise", "data": "synthetic",
-        "config": {"workload": f"single function n={n}, ON ~ Bernoulli({P_ON}), seed 1+rank, no don't-cares; "
+        "config": {"workload": f"single function n={n}, ON ~ Bernoulli({p_on}), seed 1+rank, no don't-cares; "
                                f"step = full sweep + bitmap + count + (mask,value) list, inputs resident in HBM",
                    "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state %.2f GB and bitmap %.2f GB >> 129 MB L2" % (
                        dqmc.dqmc_workspace_bytes(n) / 1e9, A / 1e9),
@@ -362,11 +367,51 @@ def run_ours(args, rank, world, local):
         result["e2e"] = e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_side:
+        result["batched"] = batched_summary(args, local)
+        result["serving"] = serving_summary(args, local)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def batched_summary(args, local):
+    """The batched workload (65,536 functions) as a compact object of the main
+    line: one graph launch per step against one dqmc_primes_dev call per
+    function, built-in launch table (the autotuner's choice on a GB300)."""
+    a = argparse.Namespace(**vars(args))
+    a.batch, a.batch_n, a.no_autotune, a.no_one_by_one, a.no_e2e = 65536, None, True, False, True
+    a.steps, a.warmup = 10, 3
+    r = run_batched(a, 0, 1, local, emit=False)
+    return {"metric": r["metric"], "value": r["value"], "unit": r["unit"], "ms_per_step": r["ms_per_step"],
+            "steps": a.steps, "one_launch_per_function": r["one_launch_per_function"],
+            "speedup_vs_one_launch_per_function": r["speedup_vs_one_launch_per_function"],
+            "results_identical": r["results_identical"], "cubes_per_s": r["cubes_per_s"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "config": r["config"]}
+
+
+def serving_summary(args, local):
+    """The serving workload at 1e4 and 1e5 arrivals/s (1000 jobs each) and
+    the small-job stream (4000 jobs), continuous batching against one job at
+    a time, as a compact object of the main line."""
+    a = argparse.Namespace(**vars(args))
+    a.serve_jobs = 1000
+    r = run_serving(a, 0, 1, local, rates=[1e4, 1e5], emit=False)
+    keep = ("jobs_per_s", "p50_ms", "p99_ms")
+    rates = [{"rate_jobs_per_s": x["rate_jobs_per_s"], "jobs": x["jobs"],
+              "continuous": {k: x["continuous"][k] for k in keep},
+              "one_by_one": {k: x["one_by_one"][k] for k in keep},
+              "throughput_speedup": x["throughput_speedup"], "p99_speedup": x["p99_speedup"],
+              "counts_identical": x["counts_identical"]} for x in r["per_rate"]]
+    sm = r["small_jobs"]
+    small = {"jobs": sm["jobs"], "n": sm["n"], "rate_jobs_per_s": sm["rate_jobs_per_s"],
+             "continuous": {k: sm["continuous"][k] for k in keep},
+             "one_by_one": {k: sm["one_by_one"][k] for k in keep},
+             "throughput_speedup": sm["throughput_speedup"], "counts_identical": sm["counts_identical"]}
+    return {"metric": "served jobs/s, continuous batching vs one job at a time", "unit": "jobs/s",
+            "per_rate": rates, "small_jobs": small, "config": r["config"]}
 
 
 def e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier):
@@ -401,9 +446,10 @@ def e2e_measure(args, n, on, cap, buf, dqmc, torch, K, world, local, barrier):
             "api": "dqmc_list (host buffers, pinned)"}
 
 
-def run_batched(args, rank, world, local):
+def run_batched(args, rank, world, local, emit=True):
     """Batched workload: one graph launch for the whole batch against one
-    dqmc_primes_dev call per function, same device buffers."""
+    dqmc_primes_dev call per function, same device buffers.  Returns the
+    result line (printed by rank 0 when emit)."""
     import numpy as np
     import torch
 
@@ -468,7 +514,7 @@ def run_batched(args, rank, world, local):
 
     if args.no_one_by_one:
         return report_batched(args, rank, world, b, nf, ns, total, ms, clocks, None, None, True, tune_s, tune_ms,
-                              table, None)
+                              table, None, emit)
 
     # one launch sequence per function (dqmc_primes_dev), same buffers
     work_bytes = max(dqmc.dqmc_workspace_bytes(int(n)) for n in set(ns.tolist()))
@@ -511,11 +557,11 @@ def run_batched(args, rank, world, local):
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / K
     return report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, same, False, tune_s, tune_ms,
-                          table, e2e_s)
+                          table, e2e_s, emit)
 
 
 def report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, same, skipped, tune_s, tune_ms,
-                   table, e2e_s):
+                   table, e2e_s, emit=True):
     K = args.steps
     cubes = int(sum(3 ** int(n) for n in ns))
     value = world * nf / (ms / 1e3)
@@ -545,9 +591,9 @@ def report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, s
         "clocks": clocks,
         "gpu_launches": K * launches_per_graph(ns, table),
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(result), flush=True)
-    return 0
+    return result
 
 
 def launches_per_graph(ns, table):
@@ -561,7 +607,10 @@ def launches_per_graph(ns, table):
     return k
 
 
-def run_serving(args, rank, world, local):
+def run_serving(args, rank, world, local, rates=None, emit=True):
+    """Serving workload (continuous batching against one job at a time) at
+    the given arrival rates; returns the result line (printed by rank 0 when
+    emit)."""
     import numpy as np
     import torch
 
@@ -571,7 +620,7 @@ def run_serving(args, rank, world, local):
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     dqmc.lib()
-    rates = [1e2, 1e3, 1e4, 1e5]
+    rates = rates or [1e2, 1e3, 1e4, 1e5]
     m_max = args.serve_jobs
     req = synth.serving_requests(m_max, 1 + rank, rate=1.0)   # n, density, seed per job (times rescaled below)
     ns = req["n"].astype(np.uint32)
@@ -635,9 +684,9 @@ def run_serving(args, rank, world, local):
         "per_rate": per_rate,
         "small_jobs": small,
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(result), flush=True)
-    return 0
+    return result
 
 
 def main():
@@ -646,9 +695,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload == "batched":
-        return run_batched(args, rank, world, local)
+        run_batched(args, rank, world, local)
+        return 0
     if args.workload == "serving":
-        return run_serving(args, rank, world, local)
+        run_serving(args, rank, world, local)
+        return 0
     return run_ours(args, rank, world, local)
 
 

@@ -109,6 +109,27 @@ int dqmc_count(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
 int dqmc_list(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
               uint32_t *out_pairs, uint64_t cap, uint64_t *out_count);
 
+/* Flags of the *_ex entry points. */
+enum {
+    /* Sweep the complement: the prime implicants of not-f, whose implicants
+     * are taken over (not ON) u DC (a don't-care of f is one of not-f too).
+     * Their disjunction is the complete sum of not-f, so De Morgan turns them
+     * into the clauses of f's prime CNF: clause k is the OR over the literals
+     * of prime k with each literal negated (Section 1, the DNF / CNF
+     * duality of the Quine-McCluskey problem). */
+    DQMC_COMPLEMENT = 1
+};
+
+/* dqmc_primes / dqmc_count with flags (0 or DQMC_COMPLEMENT; any other bit:
+ * DQMC_EINVAL).  out_prime_bitmap and out_count may each be NULL. */
+int dqmc_primes_ex(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+                   uint32_t flags, uint8_t *out_prime_bitmap, uint64_t *out_count);
+
+/* dqmc_list with flags (as dqmc_primes_ex). */
+int dqmc_list_ex(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+                 uint32_t flags, uint32_t *out_pairs, uint64_t cap,
+                 uint64_t *out_count);
+
 /* Free the device buffers cached by the host API on the current device.  It
  * waits for a host call in progress on that device; a later call allocates
  * them again.  The device's stream and count word stay until exit. */
@@ -139,6 +160,18 @@ int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc,
                   void *d_bitmap, uint32_t *d_pairs, uint64_t cap,
                   uint64_t *d_count, void *d_work, uint64_t work_bytes,
                   void *stream);
+
+/* dqmc_primes_dev and dqmc_list_dev with flags (0 or DQMC_COMPLEMENT; any
+ * other bit: DQMC_EINVAL).  With DQMC_COMPLEMENT the first pass reads the
+ * same truth tables and forms the support (not ON) u DC on the fly: no other
+ * input is read or written. */
+int dqmc_primes_dev_ex(uint32_t n, const void *d_on, const void *d_dc,
+                       uint32_t flags, void *d_bitmap, uint64_t *d_count,
+                       void *d_work, uint64_t work_bytes, void *stream);
+int dqmc_list_dev_ex(uint32_t n, const void *d_on, const void *d_dc,
+                     uint32_t flags, void *d_bitmap, uint32_t *d_pairs,
+                     uint64_t cap, uint64_t *d_count, void *d_work,
+                     uint64_t work_bytes, void *stream);
 
 /* Synchronises `stream`, then reports how the last sweep that used d_work
  * ended: DQMC_OK; DQMC_ETIMEOUT when a bounded device wait of the sweep (the

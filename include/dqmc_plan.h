@@ -39,7 +39,10 @@ extern "C" {
  *       B (inner digits 0 .. B-1, carried for contiguous rows); merge, reduce
  *       (0/1: the pass merges / reduces its group digits); chunk_mask (bit i:
  *       the pass reduces chunk digit i); out (the pass writes the bitmap, the
- *       count and the list); tiles; fix (unused, empty). */
+ *       count and the list); nbr_a, nbr_K (bitmap pass: high digits nbr_a ..
+ *       nbr_a+nbr_K-1 are reduced there too, each cell against its '*'
+ *       neighbours in those digits read from the state as the previous pass
+ *       left it; nbr_K = 0: none); tiles; fix (unused, empty). */
 int dqmc_plan_json(uint32_t n, char *buf, uint64_t cap);
 
 /* Number of passes (kernel launches of the sweep) for n variables, or

@@ -32,11 +32,18 @@ uint64_t bitmap_alloc_bytes(int n) { return align_up((pow3(n) + 7) / 8, 16); }
 //   merge       Merge G1 .. G(last-1), sparse rows in and out
 //   merge-last  Merge the last group, then Reduce it (and chunk digits
 //               {0, 1, 2} when there is no middle group)
-//   reduce      Reduce the middle groups, top down; the first of them also
-//               Reduces chunk digits {0, 1, 2}
-//   out         Reduce G0 and chunk digits {3, 4}, write the dense bitmap,
-//               the count and the list.
+//   reduce      Reduce the middle groups above G1, top down; the first of
+//               them also Reduces chunk digits {0, 1, 2}
+//   out         Reduce G1 (each cell against its '*' neighbours in G1 read
+//               from the neighbour tiles in the state, as the previous pass
+//               left it), G0 and chunk digits {3, 4} (all five when no reduce
+//               pass took {0, 1, 2}), write the dense bitmap, the count and
+//               the list.
 // Every digit is merged once before any Reduce and reduced exactly once.
+// G1 needs no pass of its own: a tile of the out pass holds G0, and the rows
+// of its G1 neighbours are whole tiles of the same shape (3^7 contiguous
+// rows), 3^j tiles away for G1 digit 7 + j; the 3^(7+K1) rows that share the
+// higher digits (51 MB at K1 = 6) stay in L2 while their tiles are swept.
 
 static FixedDigits fixed_of(const std::vector<int> &digits, const std::vector<bool> &merged)
 {
@@ -138,18 +145,22 @@ Plan make_plan(int n)
         push(sp);
         for (int d = a; d < a + K; ++d) merged[d] = true;
     }
-    for (int i = ng - 2; i >= 0; --i) {   // reduce the middle groups, top down
+    for (int i = ng - 2; i >= 1; --i) {   // reduce the middle groups above G1, top down
         const int a = starts[i], K = sizes[i], B = kTileDigits - K;
         SuperPassDesc sp = make_pass(kLoadFull, a, K, B, H, merged);
         sp.ph[0].reduce = 1;
         sp.ph[0].chunk_mask = (i == ng - 2) ? 0x07 : 0;
         push(sp);
     }
-    {   // out: G0, the bitmap, the count and the list
+    {   // out: G1 from the neighbour tiles, G0, the bitmap, the count and the list
         SuperPassDesc sp = make_pass(kLoadFull, 0, kTileDigits, 0, H, merged);
         sp.ph[0].reduce = 1;
         sp.ph[0].out = 1;
-        sp.ph[0].chunk_mask = 0x18;
+        sp.ph[0].chunk_mask = (ng == 2) ? 0x1f : 0x18;   // ng == 2: no reduce pass took {0, 1, 2}
+        if (ng >= 2) {
+            sp.ph[0].nbr_a = starts[0];
+            sp.ph[0].nbr_K = sizes[0];
+        }
         push(sp);
     }
     p.n_done = 0;
@@ -188,7 +199,8 @@ std::string describe_plan(const Plan &p)
         char buf[256];
         snprintf(buf, sizeof buf,
                  "{\"kind\":\"whole\",\"n_sb\":1,\"window\":1,\"sb\":[],\"phases\":[{\"load\":\"tt\",\"K\":%d,"
-                 "\"B\":0,\"a\":0,\"merge\":1,\"reduce\":1,\"chunk_mask\":%d,\"out\":1,\"tiles\":1,\"fix\":[]}]}",
+                 "\"B\":0,\"a\":0,\"merge\":1,\"reduce\":1,\"chunk_mask\":%d,\"out\":1,\"nbr_a\":0,\"nbr_K\":0,"
+                 "\"tiles\":1,\"fix\":[]}]}",
                  q.K, (1 << p.C) - 1);
         s += buf;
     }
@@ -204,8 +216,9 @@ std::string describe_plan(const Plan &p)
             char buf[256];
             snprintf(buf, sizeof buf,
                      "%s{\"load\":\"%s\",\"K\":%d,\"B\":%d,\"a\":%d,\"merge\":%d,\"reduce\":%d,\"chunk_mask\":%d,"
-                     "\"out\":%d,\"tiles\":%u,\"fix\":",
-                     k ? "," : "", loads[q.load], q.K, q.B, q.a, q.merge, q.reduce, q.chunk_mask, q.out, q.tiles);
+                     "\"out\":%d,\"nbr_a\":%d,\"nbr_K\":%d,\"tiles\":%u,\"fix\":",
+                     k ? "," : "", loads[q.load], q.K, q.B, q.a, q.merge, q.reduce, q.chunk_mask, q.out, q.nbr_a,
+                     q.nbr_K, q.tiles);
             s += buf + fixed_json(q.fix) + "}";
         }
         s += "]}";
@@ -406,8 +419,10 @@ static int check_dev_args(uint32_t n, const void *d_on, const void *d_dc, const 
 
 static int sweep_dev(uint32_t n, int first, int last, const void *d_on, const void *d_dc, void *d_bitmap,
                      uint64_t *d_count, void *d_work, uint64_t work_bytes, void *stream,
-                     uint32_t *d_pairs = nullptr, uint64_t cap = 0)
+                     uint32_t *d_pairs = nullptr, uint64_t cap = 0, uint32_t flags = 0)
 {
+    if (flags & ~(uint32_t)DQMC_COMPLEMENT) return DQMC_EINVAL;
+    const uint32_t inv = (flags & DQMC_COMPLEMENT) ? ~0u : 0u;
     int st = check_dev_args(n, d_on, d_dc, d_work, work_bytes);
     if (st) return st;
     if (!d_bitmap || !aligned(d_bitmap, 16)) return DQMC_EINVAL;
@@ -422,9 +437,10 @@ static int sweep_dev(uint32_t n, int first, int last, const void *d_on, const vo
                                       : reinterpret_cast<unsigned long long *>(base + w.count_off);
     if (plan.sps.empty())
         return map_cuda(launch_sweep(plan, d_on, d_dc, base + w.state_off, static_cast<uint32_t *>(d_bitmap),
-                                     cnt, static_cast<cudaStream_t>(stream), first, last));
+                                     cnt, static_cast<cudaStream_t>(stream), first, last, nullptr, inv));
     return map_cuda(launch_super(plan, d_on, d_dc, base + w.state_off, static_cast<uint32_t *>(d_bitmap), cnt,
-                                 d_pairs, cap, base + w.ctrl_off, static_cast<cudaStream_t>(stream), first, last));
+                                 d_pairs, cap, base + w.ctrl_off, static_cast<cudaStream_t>(stream), first, last,
+                                 nullptr, inv));
 }
 
 extern "C" int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
@@ -495,17 +511,30 @@ extern "C" int dqmc_compact_dev(uint32_t n, const void *d_bitmap, uint32_t *d_pa
                                    static_cast<cudaStream_t>(stream)));
 }
 
-extern "C" int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
-                             uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work,
-                             uint64_t work_bytes, void *stream)
+extern "C" int dqmc_primes_dev_ex(uint32_t n, const void *d_on, const void *d_dc, uint32_t flags, void *d_bitmap,
+                                  uint64_t *d_count, void *d_work, uint64_t work_bytes, void *stream)
+{
+    return sweep_dev(n, 0, -1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream, nullptr, 0, flags);
+}
+
+extern "C" int dqmc_list_dev_ex(uint32_t n, const void *d_on, const void *d_dc, uint32_t flags, void *d_bitmap,
+                                uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work,
+                                uint64_t work_bytes, void *stream)
 {
     if (!d_count || (cap && !d_pairs) || (d_pairs && !aligned(d_pairs, 8))) return DQMC_EINVAL;
     if (n <= DQMC_MAX_N && !make_plan((int)n).sps.empty())  // the bitmap pass also writes the list
         return sweep_dev(n, 0, -1, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream,
-                         cap ? d_pairs : nullptr, cap);
-    int st = dqmc_primes_dev(n, d_on, d_dc, d_bitmap, d_count, d_work, work_bytes, stream);
+                         cap ? d_pairs : nullptr, cap, flags);
+    int st = dqmc_primes_dev_ex(n, d_on, d_dc, flags, d_bitmap, d_count, d_work, work_bytes, stream);
     if (st) return st;
     return dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
+}
+
+extern "C" int dqmc_list_dev(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
+                             uint32_t *d_pairs, uint64_t cap, uint64_t *d_count, void *d_work,
+                             uint64_t work_bytes, void *stream)
+{
+    return dqmc_list_dev_ex(n, d_on, d_dc, 0, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, stream);
 }
 
 extern "C" int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *stream)
@@ -524,9 +553,9 @@ extern "C" int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_byt
 
 // Host entry points: copy in, run, copy out, wait.
 static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, uint8_t *out_bitmap,
-                    uint32_t *out_pairs, uint64_t cap, uint64_t *out_count, bool want_list)
+                    uint32_t *out_pairs, uint64_t cap, uint64_t *out_count, bool want_list, uint32_t flags = 0)
 {
-    if (n > DQMC_MAX_N || !on_bits) return DQMC_EINVAL;
+    if (n > DQMC_MAX_N || !on_bits || (flags & ~(uint32_t)DQMC_COMPLEMENT)) return DQMC_EINVAL;
     if (want_list && cap && !out_pairs) return DQMC_EINVAL;
     int st = DQMC_OK;
     DeviceCache *c = cache_for_current_device(&st);
@@ -563,11 +592,11 @@ static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, 
     if (e != cudaSuccess) return map_cuda(e);
     uint64_t *dcount = reinterpret_cast<uint64_t *>(c->d_count);
     if (want_list)
-        st = dqmc_list_dev(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, c->buf[2], d_pairs, cap, dcount, c->buf[3],
-                           c->cap[3], s);
+        st = dqmc_list_dev_ex(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, flags, c->buf[2], d_pairs, cap, dcount,
+                              c->buf[3], c->cap[3], s);
     else
-        st = dqmc_primes_dev(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, c->buf[2], dcount, c->buf[3],
-                             c->cap[3], s);
+        st = dqmc_primes_dev_ex(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, flags, c->buf[2], dcount, c->buf[3],
+                                c->cap[3], s);
     if (st) return st;
     e = cudaMemcpyAsync(c->h_count, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && out_bitmap)
@@ -604,6 +633,18 @@ extern "C" int dqmc_list(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_b
                          uint64_t cap, uint64_t *out_count)
 {
     return host_run(n, on_bits, dc_bits, nullptr, out_pairs, cap, out_count, true);
+}
+
+extern "C" int dqmc_primes_ex(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, uint32_t flags,
+                              uint8_t *out_prime_bitmap, uint64_t *out_count)
+{
+    return host_run(n, on_bits, dc_bits, out_prime_bitmap, nullptr, 0, out_count, false, flags);
+}
+
+extern "C" int dqmc_list_ex(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, uint32_t flags,
+                            uint32_t *out_pairs, uint64_t cap, uint64_t *out_count)
+{
+    return host_run(n, on_bits, dc_bits, nullptr, out_pairs, cap, out_count, true, flags);
 }
 
 extern "C" void dqmc_release(void)

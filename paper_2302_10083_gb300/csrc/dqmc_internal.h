@@ -63,6 +63,11 @@ struct PhaseDesc {
     int reduce = 0;                 // Reduce the group digits
     int chunk_mask = 0;             // chunk digits Reduced here (bit i = chunk digit i)
     int out = 0;                    // write the dense bitmap (+ count, + list) instead of rows
+    // Neighbour group (out phase only): high digits nbr_a .. nbr_a+nbr_K-1 are
+    // also reduced here, each cell against its '*' neighbours in those digits
+    // as the previous pass left them in the state (the neighbour tiles are
+    // read from device memory; nbr_K = 0: none).
+    int nbr_a = 0, nbr_K = 0;
     uint32_t tiles = 1;             // tiles per super-block = product of fix.r
     FixedDigits fix;                // super-block digits fixed per tile
 };
@@ -137,11 +142,12 @@ struct BatchArgs {
 // Enqueue the whole sweep.  d_count must point to a uint64 (zeroed here).
 // Passes [first, last) only (0 .. passes.size() for the whole sweep); pass 0
 // zeroes *d_count first.  With a batch (n <= 12), one CTA per function and
-// d_on / d_dc / d_bitmap / d_count are unused.
+// d_on / d_dc / d_bitmap / d_count are unused.  tt_invert = ~0u sweeps the
+// complement: the support is (not ON) or DC instead of ON or DC.
 cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc,
                          void *d_state, uint32_t *d_bitmap, unsigned long long *d_count,
                          cudaStream_t stream, int first = 0, int last = -1,
-                         const BatchArgs *batch = nullptr);
+                         const BatchArgs *batch = nullptr, uint32_t tt_invert = 0);
 
 // Bytes pass i moves by design (rows read and written x 32, truth tables, bitmap).
 uint64_t pass_bytes(const Plan &plan, int i, bool with_dc);
@@ -170,7 +176,7 @@ constexpr uint32_t kErrBounds = 0x424f554eu;   // "BOUN"
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
                          uint32_t *d_bitmap, unsigned long long *d_count, uint32_t *d_pairs,
                          uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last,
-                         const BatchArgs *batch = nullptr);
+                         const BatchArgs *batch = nullptr, uint32_t tt_invert = 0);
 
 // Test hook: a device wait on a counter nothing sets; it must time out.
 cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wait_ns, cudaStream_t stream);

@@ -106,6 +106,7 @@ static __device__ const PassTables g_tab = make_pass_tables();
 struct PassParams {
     const uint32_t *on;
     const uint32_t *dc;
+    uint32_t inv;               // ~0u: sweep the complement (support = (not ON) or DC)
     uint4 *state;
     uint32_t *out;
     unsigned long long *count;
@@ -119,6 +120,9 @@ struct PassParams {
     uint64_t w_g;               // 3^a
     uint32_t nmask;             // (1 << n) - 1
     int H, slot;
+    // bitmap pass: the first nbr_k fixed digits (high digits 7 .. 6+nbr_k) are
+    // reduced against the '*' neighbour tiles read from the state (0: none)
+    int nbr_k;
     FixedDigits fix;            // digits fixed per tile, ascending
     // Batch mode (bfn non-null): block b works on tile b % tiles_per_fn of
     // function bfn[b / tiles_per_fn]; its truth tables, bitmap and count come
@@ -159,6 +163,7 @@ __device__ __forceinline__ FnBufs fn_bufs(const PassParams &P)
     return f;
 }
 
+constexpr int kMaxNbr = 6;          // neighbour-group digits of the bitmap pass
 constexpr int kThreads = 256;       // threads per CTA of the first pass
 constexpr int kOutStepDigits = 3;   // bitmap pass: tile digits reduced per step
 constexpr int kOutThreads = 384;    // threads per CTA of the bitmap pass and the Merge-only passes
@@ -351,6 +356,8 @@ struct PassShared {
     uint32_t warp_tot[kMaxWarps];
     uint32_t rcnt[32];                    // primes per 32-unit region (bitmap pass)
     uint32_t tile_mask, tile_val;         // literal / value bits of the digits fixed per tile
+    uint32_t nbr_off[kMaxNbr];            // bitmap pass: '*' neighbour tiles, uint4 offsets from the tile
+    int n_nbr;
     int list_ok, overflow, next_region, load_fail;
     uint16_t c5[243];                     // copy of the chunk-cell table
     uint16_t code[kUnits];                // copy of the unit-digit table
@@ -370,11 +377,13 @@ __device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S,
     if (kTicket && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
     uint64_t base = 0, ttb = 0;
     uint32_t m = 0, vv = 0;
+    uint32_t dlo = 0;   // 2 bits per digit: values of the first kMaxNbr fixed digits
     auto put = [&](int i, uint32_t d) {
         base += d * f.w3[i];
         ttb += d * f.w2[i];
         if (d != 2) m |= 1u << (kChunkDigits + f.j[i]);
         if (d == 1) vv |= 1u << (kChunkDigits + f.j[i]);
+        if (i < kMaxNbr) dlo |= d << (2 * i);
     };
     if (t >> 32) {
         uint64_t x = t;
@@ -410,6 +419,17 @@ __device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S,
     S.tile = t;
     S.tile_mask = m;
     S.tile_val = vv;
+    // The '*' neighbour of this tile in each neighbour-group digit that is
+    // 0/1 here: the tile with that digit set to '*', (2 - d) 3^j rows on.
+    int nn = 0;
+    for (int i = 0; i < P.nbr_k && i < kMaxNbr; ++i) {
+        const uint32_t d = (dlo >> (2 * i)) & 3u;
+        if (d == 2) continue;
+        const uint64_t off = (uint64_t)(2 - d) * f.w3[i];
+        if (ck(P, base + off + kTileRows <= P.state_rows && 2 * off < (1ull << 32), base + off))
+            S.nbr_off[nn++] = (uint32_t)(2 * off);
+    }
+    S.n_nbr = nn;
 }
 
 // ------------------------------------------------------------ first pass
@@ -428,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 3) tt_pass_kernel(const __grid_const
 
     for (int gb = tid; gb < (1 << kTileDigits); gb += kThreads) {
         if (!ck(P, ttb + gb < P.tt_words, ttb + gb)) continue;
-        uint32_t x = __ldg(F.on + ttb + gb);
+        uint32_t x = __ldg(F.on + ttb + gb) ^ P.inv;
         if (F.dc) x |= __ldg(F.dc + ttb + gb);
         uint32_t v[kChunkWords];
         chunk_from_word_p(x, v);
@@ -697,12 +717,36 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
             // any) and counts them.
             const SubSync sync{1, NT, true};
             reduce_all<kTileDigits, 0, kOutStepDigits>(tile, tid, NT, sync);
+            // Neighbour group (bitmap pass): a cell is also cleared when its
+            // '*' neighbour in a neighbour-group digit is set in the state as
+            // the previous pass left it.  The neighbour tiles are never
+            // written by this pass, so every tile reads them unchanged; the
+            // result is exact in any order with the tile's own Reduce steps
+            // (a set cell is always an implicant, and a cell with an implicant
+            // extension in such a digit finds it still set: clearing that
+            // extension would take an implicant extension of the cell in an
+            // earlier group).
+            // A row with no set cell stays empty whatever its neighbours
+            // hold, so it reads no neighbour row and skips the chunk digits
+            // (the tile itself is always read and its bitmap always written).
+            const int n_nbr = (MODE == kModeOut) ? S.n_nbr : 0;
+            const uint4 *const tile_g = state + 2 * base;
             for (int r = tid; r < kTileRows; r += NT) {
                 const uint4 q0 = tile[2 * r], q1 = tile[2 * r + 1];
                 uint32_t v[kChunkWords] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-                if constexpr (CM != 0) {
+                const bool any = ((q0.x | q0.y | q0.z | q0.w) | (q1.x | q1.y | q1.z | q1.w)) != 0u;
+                if (any && (CM != 0 || n_nbr)) {
                     uint32_t acc[kChunkWords] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-                    chunk_reduce_p<CM>(v, acc);
+#pragma unroll
+                    for (int k = 0; k < kMaxNbr; ++k) {
+                        if (k < n_nbr) {
+                            const uint4 *src = tile_g + S.nbr_off[k] + 2 * r;
+                            const uint4 a0 = __ldcg(src), a1 = __ldcg(src + 1);
+                            acc[0] |= a0.x; acc[1] |= a0.y; acc[2] |= a0.z; acc[3] |= a0.w;
+                            acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
+                        }
+                    }
+                    if constexpr (CM != 0) chunk_reduce_p<CM>(v, acc);
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
                     tile[2 * r] = make_uint4(v[0], v[1], v[2], v[3]);     // only this thread touches row r here
@@ -980,17 +1024,25 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 // Threads per CTA and digits per step (measured at n = 24: the last Merge
 // pass 14.70 ms with 384 threads and 2 digits, 14.81 with 384 and 3; the
 // middle Reduce pass 14.78 ms with 256 and 2, 17.26 with 384 and 3).
-template <bool MERGE> constexpr int mr_threads() { return MERGE ? 384 : 256; }
+// A wide tile (HL = K + B = 8 tile digits, 3^8 rows, 210 KB: one CTA per SM
+// with 1024 threads) carries two inner digits, so its rows go out in runs of
+// nine (288 bytes) instead of three.
+template <bool MERGE, int HL = kTileDigits>
+constexpr int mr_threads() { return HL > kTileDigits ? 1024 : (MERGE ? 384 : 256); }
+template <int HL> constexpr int mr_blocks() { return HL > kTileDigits ? 1 : 3; }
 constexpr int kMrDigits = 2;
 
 template <int K, int B, int CM, bool STAGE, bool MERGE>
-__global__ void __launch_bounds__(mr_threads<MERGE>(), 3) mr_pass_kernel(const __grid_constant__ PassParams P)
+__global__ void __launch_bounds__(mr_threads<MERGE, K + B>(), mr_blocks<K + B>())
+    mr_pass_kernel(const __grid_constant__ PassParams P)
 {
-    constexpr int NT = mr_threads<MERGE>();
-    constexpr int R = kTileRows;
+    constexpr int HL = K + B;           // tile digits
+    constexpr int NT = mr_threads<MERGE, HL>();
+    constexpr int R = (int)pow3(HL);
     constexpr int RE = (int)pow3(B);   // inner rows per group-digit value
     constexpr int NB = 1 << K;
-    static_assert(K + B == kTileDigits && B >= 1, "tiles are 3^7 rows with at least one inner digit");
+    static_assert((HL == kTileDigits || HL == kTileDigits + 1) && B >= 1,
+                  "tiles are 3^7 or 3^8 rows with at least one inner digit");
     extern __shared__ uint4 tile[];
     __shared__ PassShared S;
     const int tid = threadIdx.x;
@@ -1026,8 +1078,8 @@ __global__ void __launch_bounds__(mr_threads<MERGE>(), 3) mr_pass_kernel(const _
     const SubSync sync{1, NT, true};
     __syncthreads();
 
-    if constexpr (MERGE) merge_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
-    reduce_all<kTileDigits, B, kMrDigits>(tile, tid, NT, sync);
+    if constexpr (MERGE) merge_all<HL, B, kMrDigits>(tile, tid, NT, sync);
+    reduce_all<HL, B, kMrDigits>(tile, tid, NT, sync);
 
     // chunk digits, then out
     for (int ri = tid; ri < R; ri += NT) {
@@ -1083,14 +1135,15 @@ static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t
                         unit_threads<MODE>());
 }
 
-template <int K, int CM, bool MERGE>
+template <int K, int CM, bool MERGE, int HL = kTileDigits>
 static cudaError_t launch_mr(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
-    constexpr int B = kTileDigits - K;
-    const size_t smem = (size_t)kTileRows * kChunkBytes;
+    constexpr int B = HL - K;
+    const size_t smem = (size_t)pow3(HL) * kChunkBytes;
+    constexpr int NT = mr_threads<MERGE, HL>();
     if (p.w_g * kChunkBytes >= kStageStrideBytes)
-        return launch_tiles(mr_pass_kernel<K, B, CM, true, MERGE>, smem, p, tiles, stream, mr_threads<MERGE>());
-    return launch_tiles(mr_pass_kernel<K, B, CM, false, MERGE>, smem, p, tiles, stream, mr_threads<MERGE>());
+        return launch_tiles(mr_pass_kernel<K, B, CM, true, MERGE>, smem, p, tiles, stream, NT);
+    return launch_tiles(mr_pass_kernel<K, B, CM, false, MERGE>, smem, p, tiles, stream, NT);
 }
 
 template <int CM, bool MERGE>
@@ -1123,7 +1176,7 @@ static cudaError_t dispatch_group(int K, const PassParams &p, uint64_t tiles, cu
 
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state, uint32_t *d_bitmap,
                          unsigned long long *d_count, uint32_t *d_pairs, uint64_t cap, void *d_ctrl,
-                         cudaStream_t stream, int first, int last, const BatchArgs *batch)
+                         cudaStream_t stream, int first, int last, const BatchArgs *batch, uint32_t tt_invert)
 {
     const CtrlLayout cl = ctrl_layout(plan);
     cudaError_t e = cudaSuccess;
@@ -1140,6 +1193,7 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
     PassParams a{};
     a.on = static_cast<const uint32_t *>(d_on);
     a.dc = static_cast<const uint32_t *>(d_dc);
+    a.inv = tt_invert;
     a.state = static_cast<uint4 *>(d_state);
     a.out = d_bitmap;
     a.count = d_count;
@@ -1172,16 +1226,26 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
         a.w_g = pow3(ph.a);
         a.slot = sp.slot;
         a.fix = sp.sb;
+        a.nbr_k = ph.out ? ph.nbr_K : 0;   // the neighbour group is the first nbr_K fixed digits (7 ..)
         a.tiles_per_fn = (uint32_t)sp.n_sb;
         const uint64_t tiles = sp.n_sb * (batch ? batch->nfun : 1u);
         if (ph.load == kLoadTT)
             e = (ph.K == kTileDigits && ph.a == 0)
                     ? launch_tiles(tt_pass_kernel, (size_t)kTileRows * kChunkBytes, a, tiles, stream)
                     : cudaErrorInvalidValue;
-        else if (ph.out && ph.K == kTileDigits && ph.a == 0 && ph.chunk_mask == 0x18)
+        else if (ph.out && (ph.K != kTileDigits || ph.a != 0 || ph.nbr_K > kMaxNbr ||
+                            (ph.nbr_K && ph.nbr_a != kTileDigits)))
+            e = cudaErrorInvalidValue;
+        else if (ph.out && ph.chunk_mask == 0x18)
             e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0x18>(a, tiles, stream);
+        else if (ph.out && ph.chunk_mask == 0x1f)
+            e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0x1f>(a, tiles, stream);
         else if (ph.out)
             e = cudaErrorInvalidValue;
+        else if (ph.merge && ph.reduce && ph.chunk_mask == 0 && ph.K + ph.B == kTileDigits + 1)
+            e = (ph.K == 6) ? launch_mr<6, 0, true, kTileDigits + 1>(a, tiles, stream) : cudaErrorInvalidValue;
+        else if (ph.K + ph.B != kTileDigits)
+            e = cudaErrorInvalidValue;      // wide tiles: only the last Merge pass of six digits
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0)
             e = dispatch_mr<0, true>(ph.K, a, tiles, stream);
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x07)

@@ -38,6 +38,7 @@ static __constant__ MaskTable kMasks = make_mask_table();
 struct PassArgs {
     const uint32_t *on;
     const uint32_t *dc;
+    uint32_t inv;               // ~0u: sweep the complement (support = (not ON) or DC)
     uint4 *state;               // 2 x uint4 per row
     uint32_t *out;              // dense bitmap words
     unsigned long long *count;
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
             uint32_t x;
             if constexpr (C == kChunkDigits) {
                 const uint64_t wi = topi * NB + gb;
-                x = __ldg(p_on + wi);
+                x = __ldg(p_on + wi) ^ p.inv;
                 if (p_dc) x |= __ldg(p_dc + wi);
             } else {
                 const uint8_t *on8 = reinterpret_cast<const uint8_t *>(p_on);
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) tile_pass(const PassArgs p)
                 // 2^C <= 16 minterms: one byte, two for C = 4
                 x = on8[0];
                 if constexpr (C == 4) x |= (uint32_t)on8[1] << 8;
+                x ^= p.inv;   // bits past 2^C are masked below
                 if (dc8) {
                     x |= dc8[0];
                     if constexpr (C == 4) x |= (uint32_t)dc8[1] << 8;
@@ -416,7 +418,7 @@ static cudaError_t dispatch_k(int C, const Pass &ps, const PassArgs &a, cudaStre
 
 cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
                          uint32_t *d_bitmap, unsigned long long *d_count, cudaStream_t stream, int first,
-                         int last, const BatchArgs *batch)
+                         int last, const BatchArgs *batch, uint32_t tt_invert)
 {
     if (last < 0) last = (int)plan.passes.size();
     if (first < 0 || last > (int)plan.passes.size() || first > last) return cudaErrorInvalidValue;
@@ -429,6 +431,7 @@ cudaError_t launch_sweep(const Plan &plan, const void *d_on, const void *d_dc, v
     PassArgs a{};
     a.on = static_cast<const uint32_t *>(d_on);
     a.dc = static_cast<const uint32_t *>(d_dc);
+    a.inv = tt_invert;
     a.state = static_cast<uint4 *>(d_state);
     a.out = d_bitmap;
     a.count = d_count;

@@ -25,6 +25,7 @@ DQMC_ETRUNC = -3
 DQMC_ECUDA = -4
 DQMC_ETIMEOUT = -5
 DQMC_MAX_N = 25
+DQMC_COMPLEMENT = 1   # flag of the *_ex entry points: the primes of not-f
 
 _lock = threading.Lock()
 _lib = None
@@ -50,6 +51,13 @@ _SIGS = {
     "dqmc_primes": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u8p]),
     "dqmc_count": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u64p]),
     "dqmc_list": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u32p, ctypes.c_uint64, c_u64p]),
+    "dqmc_primes_ex": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, ctypes.c_uint32, c_u8p, c_u64p]),
+    "dqmc_list_ex": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, ctypes.c_uint32, c_u32p, ctypes.c_uint64,
+                                    c_u64p]),
+    "dqmc_primes_dev_ex": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, ctypes.c_uint32, c_vp, c_vp, c_vp,
+                                          ctypes.c_uint64, c_vp]),
+    "dqmc_list_dev_ex": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, ctypes.c_uint32, c_vp, c_vp, ctypes.c_uint64,
+                                        c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_release": (None, []),
     "dqmc_primes_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_list_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp,
@@ -219,6 +227,28 @@ def dqmc_list(n: int, on_bits, dc_bits=None, cap: int | None = None):
         if not (auto and st == DQMC_ETRUNC):
             break
         cap = int(c.value)
+    k = min(int(c.value), cap)
+    return out[: 2 * k].reshape(k, 2), int(c.value)
+
+
+def dqmc_primes_ex(n: int, on_bits, dc_bits=None, flags: int = 0):
+    """(prime bitmap, count) through dqmc_primes_ex (flags: 0 or DQMC_COMPLEMENT)."""
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    out = np.empty(max(dqmc_bitmap_bytes(n), 1), dtype=np.uint8)
+    c = ctypes.c_uint64()
+    _check(lib().dqmc_primes_ex(n, _p8(on), _p8(dc), flags, _p8(out), ctypes.byref(c)), "dqmc_primes_ex")
+    return out[: dqmc_bitmap_bytes(n)], int(c.value)
+
+
+def dqmc_list_ex(n: int, on_bits, dc_bits=None, flags: int = 0, cap: int = 0):
+    """(pairs (k, 2) uint32, count) through dqmc_list_ex; k = min(count, cap)."""
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    out = np.empty(2 * max(cap, 1), dtype=np.uint32)
+    c = ctypes.c_uint64()
+    st = lib().dqmc_list_ex(n, _p8(on), _p8(dc), flags, out.ctypes.data_as(c_u32p), cap, ctypes.byref(c))
+    _check(st, "dqmc_list_ex", ok=(DQMC_OK, DQMC_ETRUNC))
     k = min(int(c.value), cap)
     return out[: 2 * k].reshape(k, 2), int(c.value)
 

@@ -74,6 +74,11 @@ def test_bad_arguments_rejected_without_gpu():
     assert L.dqmc_primes_dev_static(16, 256, None, 256, None, None) == dqmc.DQMC_EINVAL
     assert L.dqmc_primes_dev_static(26, 256, None, 256, None, None) == dqmc.DQMC_EINVAL
     assert L.dqmc_dev_status_static(16, None) == dqmc.DQMC_EINVAL
+    # unknown flags of the *_ex entry points are refused before any CUDA call
+    on = np.zeros(16, dtype=np.uint8)
+    assert L.dqmc_primes_ex(4, on.ctypes.data_as(dqmc.c_u8p), None, 2, None, None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_list_ex(4, on.ctypes.data_as(dqmc.c_u8p), None, 6, None, 0, None) == dqmc.DQMC_EINVAL
+    assert L.dqmc_primes_dev_ex(14, 256, None, 2, 256, None, 256, 1 << 30, None) == dqmc.DQMC_EINVAL
 
 
 def test_batch_arguments_rejected_without_gpu():
@@ -209,6 +214,11 @@ def test_plan_digit_coverage(n):
                 # every digit is merged before the first Reduce
                 merge_done = True
                 reduced += digits
+            if ph["nbr_K"]:
+                # the neighbour group: only in the bitmap pass, and only the
+                # digits just above its tile (the first fixed digits)
+                assert ph["out"] and ph["nbr_a"] == 7 and 1 <= ph["nbr_K"] <= 6
+                reduced += list(range(ph["nbr_a"], ph["nbr_a"] + ph["nbr_K"]))
             chunk += bin(ph["chunk_mask"]).count("1")
     assert sorted(merged) == list(range(H))
     assert sorted(reduced) == list(range(H))
@@ -362,8 +372,8 @@ def test_ticket_order_is_a_valid_schedule(n):
 
 # ------------------------------------------------- semantic simulation
 
-def grouped_reduce(S, n, digits):
-    """Reduce over a set of digits, every read taken from the state as it was before."""
+def reduce_clear(S, n, digits):
+    """Cells whose '*' neighbour in one of the digits is set in S."""
     A = S.reshape((3,) * n) if n else S
     clear = np.zeros_like(A)
     for j in digits:
@@ -373,7 +383,12 @@ def grouped_reduce(S, n, digits):
             idx = [slice(None)] * n
             idx[ax] = slice(v, v + 1)
             clear[tuple(idx)] |= star
-    return (A & ~clear).reshape(-1)
+    return clear.reshape(-1)
+
+
+def grouped_reduce(S, n, digits):
+    """Reduce over a set of digits, every read taken from the state as it was before."""
+    return S & ~reduce_clear(S, n, digits)
 
 
 def merge_digit(S, n, j):
@@ -387,7 +402,7 @@ def merge_digit(S, n, j):
     return A.reshape(-1)
 
 
-@pytest.mark.parametrize("n,seed", [(8, 1), (13, 2), (14, 3), (15, 4), (16, 5)])
+@pytest.mark.parametrize("n,seed", [(8, 1), (13, 2), (14, 3), (15, 4), (16, 5), (19, 6)])
 def test_plan_schedule_simulated(n, seed):
     """Run the plan's digit schedule on the host (Merge digit by digit, Reduce
     grouped per phase from the phase's starting state) against the oracle."""
@@ -412,8 +427,12 @@ def test_plan_schedule_simulated(n, seed):
                 for j in grp:
                     S = merge_digit(S, n, j)
             red = (grp if ph["reduce"] else []) + [i for i in range(C) if (ph["chunk_mask"] >> i) & 1]
+            before = S
             if red:
                 S = grouped_reduce(S, n, red)
+            if ph["nbr_K"]:
+                # the neighbour group reads the state as the pass found it
+                S = S & ~reduce_clear(before, n, [C + d for d in range(ph["nbr_a"], ph["nbr_a"] + ph["nbr_K"])])
     want = oracle.sweep(n, on, dc) != 0
     assert np.array_equal(S, want)
 
@@ -520,7 +539,8 @@ def test_plan_json_fields_as_documented(n):
         assert set(q) == want
         assert len(q["phases"]) == 1
         ph = q["phases"][0]
-        assert set(ph) == {"load", "K", "B", "a", "merge", "reduce", "chunk_mask", "out", "tiles", "fix"}
+        assert set(ph) == {"load", "K", "B", "a", "merge", "reduce", "chunk_mask", "out", "nbr_a", "nbr_K",
+                           "tiles", "fix"}
         assert ph["load"] in ("tt", "sparse", "full") and ph["fix"] == []
         if q["kind"] == "super":
             assert q["window"] == q["step_size"] == q["n_sb"] and q["n_steps"] == q["groups"] == 1

@@ -519,3 +519,34 @@ def test_stored_digest_counts_near_expectation():
         assert len(h) == len(hl) == 64 and int(h, 16) >= 0 and int(hl, 16) >= 0
         e = bf.expected_primes(n, p_on + (1 - p_on) * p_dc)
         assert abs(count - e) / e < 0.01, (n, count, e)
+
+
+# ------------------------------------------------------ complement (CNF) mode
+
+@pytest.mark.parametrize("n,W,Wdc", [
+    (3, {2, 3}, set()),             # not-majority: primes 00*, 0*0, *00
+    (7, {4, 5, 6, 7}, set()),
+    (10, {0, 3, 4, 5, 9}, {1, 8}),
+    (11, set(range(1, 12, 2)), set()),   # not-parity is even parity
+])
+def test_complement_symmetric_closed_form(n, W, Wdc):
+    """Section 1: the primes of not-f give f's prime CNF (De Morgan).  The
+    complement of a symmetric function with ON weights W and don't-care
+    weights Wdc is symmetric with support weights ({0..n} - W) | Wdc, so its
+    primes have the same closed form.  The complement's tables are built the
+    way the library forms them: ON' = not(ON or DC), DC' = DC."""
+    on = bf.symmetric_support(n, W)
+    dc = bf.symmetric_support(n, Wdc) & ~on
+    S = oracle.sweep(n, bf.bitmap_from_bool(~on & ~dc), bf.bitmap_from_bool(dc))
+    Wc = (set(range(n + 1)) - W) | Wdc
+    assert np.array_equal(S != 0, bf.symmetric_prime_cells(n, Wc))
+    if n == 3 and not Wdc:
+        got = sorted(bf.cube_string(n, r) for r in np.nonzero(S)[0])
+        assert got == sorted(["00*", "0*0", "*00"])
+
+
+def test_complement_of_constant_zero_is_constant_one():
+    """not(0) = 1: the only prime is the all-'*' cube (Section 3)."""
+    n = 6
+    S = oracle.sweep(n, bf.bitmap_from_bool(np.ones(1 << n, dtype=bool)))
+    assert np.nonzero(S)[0].tolist() == [3 ** n - 1]
