@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--ref-n", type=int, default=REF_SAMPLE_N,
                     help="--impl reference: the n of the function the oracle sweeps per step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inplace", action="store_true",
+                    help="single workload: write the bitmap over the state (one array; n = 25 fits only so)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true",
                     help="single workload: leave out the compact batched and serving results of the line")
@@ -160,7 +162,7 @@ class ClockSampler:
 
 # The sources the streaming pass kernels are compiled from: a change to any of
 # them voids the stored ncu traffic of those kernels.
-PASS_SOURCES = ("dqmc_chunk.cuh", "dqmc_internal.h", "dqmc_pass.cu")
+PASS_SOURCES = ("dqmc_api.cu", "dqmc_chunk.cuh", "dqmc_internal.h", "dqmc_pass.cu", "dqmc_steps.cuh")
 
 
 def kernel_source_hash():
@@ -172,19 +174,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key):
-    """dram read+write bytes per launch from profiles/ncu_traffic.json, if it was
-    taken from the current kernel sources."""
+def ncu_traffic(kernel_key, n):
+    """dram read+write bytes of one launch of pass `kernel_key` at this n, from
+    profiles/ncu_traffic.json, if that capture was taken at this n from the
+    current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash() or d.get("n") != n:
         return None
-    ent = d.get("kernels", {}).get(kernel_key)
-    return None if ent is None else ent.get("bytes_per_launch_full")
+    ent = d.get("passes", {}).get(kernel_key)
+    return None if ent is None else ent["dram_read_bytes"] + ent["dram_write_bytes"]
 
 
 def single_metric(n):
@@ -271,7 +274,7 @@ def run_ours(args, rank, world, local):
     exp_primes = sum(comb(n, w) * 2 ** (n - w) * p_on ** (2 ** w) * (1 - p_on ** (2 ** w)) ** (n - w)
                      for w in range(n + 1))
     cap = int(exp_primes * 1.05) + 1024
-    buf = dqmc.DeviceBuffers(n, device=f"cuda:{local}", with_dc=False, cap=cap)
+    buf = dqmc.DeviceBuffers(n, device=f"cuda:{local}", with_dc=False, cap=cap, inplace=args.inplace)
     buf.on[: on.size].copy_(torch.from_numpy(on))
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -335,10 +338,21 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = measured_peaks()
     # dominant kernel = the sweep pass with the largest share of the step
     dom = max(range(npass), key=lambda p: per_pass[p])
-    dom_bytes = dqmc.dqmc_pass_bytes(n, dom, False)
-    achieved = dom_bytes / (per_pass[dom] / 1e3) / 1e9
     A = (cubes + 7) // 8
     b_roof = (1 << n) // 8 + 3 * A
+    # The bitmap pass must read the merged state and write the primes: 2 A
+    # bytes by the method (the padded rows and the list come on top; they are
+    # the design bytes).
+    dom_bytes = 2 * A if dom == npass - 1 else dqmc.dqmc_pass_bytes(n, dom, False)
+    achieved = dom_bytes / (per_pass[dom] / 1e3) / 1e9
+    passes = {}
+    for p in range(npass):
+        design = dqmc.dqmc_pass_bytes(n, p, False) + (8 * count if p == npass - 1 else 0)
+        tr = ncu_traffic(f"pass{p}", n)
+        passes[names[p]] = {"ms": per_pass[p], "design_bytes": design,
+                            "design_gbs": design / (per_pass[p] / 1e3) / 1e9,
+                            "traffic_bytes": tr,
+                            "traffic_gbs": None if tr is None else tr / (per_pass[p] / 1e3) / 1e9}
     result = {
         "metric": single_metric(n),
         "value": value, "unit": "cubes/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -348,17 +362,22 @@ def run_ours(args, rank, world, local):
                                f"step = full sweep + bitmap + count + (mask,value) list, inputs resident in HBM",
                    "n": n, "cubes": cubes, "primes": count, "l2": "no flush: state %.2f GB and bitmap %.2f GB >> 129 MB L2" % (
                        dqmc.dqmc_workspace_bytes(n) / 1e9, A / 1e9),
+                   "bitmap": "written over the state (one array)" if args.inplace else "a buffer of its own",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": ncu_traffic(f"pass{dom}"),
-                     "algorithmic_bytes_per_launch": dom_bytes},
+                     "traffic": ncu_traffic(f"pass{dom}", n),
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "algorithmic_bytes_note": "the method's bytes: state read + primes written, 2*ceil(3^n/8) "
+                                               "for the bitmap pass; padded rows and the list are in passes[].design_bytes"},
         "path_roofline": {"b_roof_bytes": b_roof, "achieved_gbs": b_roof / (ms / 1e3) / 1e9,
                           "frac_of_peak": b_roof / (ms / 1e3) / 1e9 / peak,
                           "frac_of_nominal": b_roof / (ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
                           "nominal_gbs": NOMINAL_HBM_GBS,
                           "note": "B_roof = 2^n/8 + 3*ceil(3^n/8): read input, write merged state, read it, write primes"},
         "per_kernel_ms": {names[p]: per_pass[p] for p in range(npass)},
+        "passes": passes,
+        "step_design_bytes": sum(x["design_bytes"] for x in passes.values()),
         "gpu_launches": K * npass,
         "clocks": clocks,
     }

@@ -61,8 +61,10 @@ enum {
     DQMC_ETIMEOUT = -5
 };
 
-/* Largest n handled: the padded state (3^(n-5) x 32 bytes) plus the bitmap of
- * n = 25 take 218 GB, which fits the 288 GB of one GB300. */
+/* Largest n handled: the padded state of n = 25 (3^20 rows of 32 bytes,
+ * 111.6 GB) holds its own bitmap (105.9 GB) when the bitmap is written over it
+ * (the host entry points do so at n = 25), well inside the 288 GB of one
+ * GB300. */
 #define DQMC_MAX_N 25
 
 /* Human-readable text for a status code (static storage, never NULL). */
@@ -130,6 +132,46 @@ int dqmc_list_ex(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
                  uint32_t flags, uint32_t *out_pairs, uint64_t cap,
                  uint64_t *out_count);
 
+/* Largest n of dqmc_sparse_list: 2n code bits plus the control flag fit
+ * 64 bits. */
+#define DQMC_SPARSE_MAX_N 30
+
+/* SparseQMC on the GPU (Section 5, "SparseQMC"; Algorithm 1 level by level):
+ * the same primes as dqmc_list, found from the support's minterms upward
+ * (level w = the implicants with w wildcards, as a list and a hash set with
+ * linear probing; a new implicant is made only at a position with no
+ * wildcard before it, then every merge pair of it is flagged redundant; the
+ * unflagged cubes of a level are prime).  Its work and memory follow the
+ * number of implicants, not 3^n, so it suits sparse functions (the paper
+ * finds it faster than the dense sweep up to about 50-60% density) and n up
+ * to DQMC_SPARSE_MAX_N.  flags: 0 or DQMC_COMPLEMENT.  out_pairs: caller-owned,
+ * 2*cap uint32, (mask, value) pairs in ascending rho as dqmc_list;
+ * *out_count receives the number of primes (DQMC_ETRUNC when it exceeds cap).
+ * Device memory is allocated for the call and freed before it returns
+ * (DQMC_ENOMEM when the levels do not fit).  Synchronous. */
+int dqmc_sparse_list(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+                     uint32_t flags, uint32_t *out_pairs, uint64_t cap,
+                     uint64_t *out_count);
+
+/* Largest n of dqmc_cover (two 32-bit words per minterm of device state). */
+#define DQMC_COVER_MAX_N 26
+
+/* The second step of the Quine-McCluskey method (Section 1: choose a subset
+ * of the prime implicants covering the function; a SetCover instance, so a
+ * heuristic): the essential primes (each the only one covering some ON
+ * minterm), then, while an ON minterm is uncovered, the prime covering the
+ * most uncovered ON minterms (ties: the lowest index).  Don't-care minterms
+ * need no cover.  This is not part of the paper's method.
+ * pairs: the primes as (mask, value) uint32 pairs (count of them), e.g. from
+ * dqmc_list or dqmc_sparse_list.  out_sel: caller-owned, count uint32,
+ * receives the selected primes' indexes in ascending order; *out_nsel their
+ * number.  DQMC_EINVAL if the given cubes do not cover the ON-set.  Device
+ * memory is allocated for the call and freed before it returns.
+ * Synchronous. */
+int dqmc_cover(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits,
+               const uint32_t *pairs, uint64_t count, uint32_t *out_sel,
+               uint64_t *out_nsel);
+
 /* Free the device buffers cached by the host API on the current device.  It
  * waits for a host call in progress on that device; a later call allocates
  * them again.  The device's stream and count word stay until exit. */
@@ -145,7 +187,12 @@ void dqmc_release(void);
 /* The prime bitmap, as dqmc_primes (Algorithm 3 of Section 4.1: MergeAll,
  * then ReduceAll; the set cells are Section 2's prime implicants).
  * d_on, d_dc: ceil(2^n/8)-byte truth tables (d_dc may be NULL).
- * d_bitmap: dqmc_bitmap_alloc_bytes(n) bytes, receives the prime bitmap.
+ * d_bitmap: dqmc_bitmap_alloc_bytes(n) bytes, receives the prime bitmap.  For
+ * n >= 13 it may be d_work itself: the bitmap is then written over the state
+ * at the start of the workspace (the state is larger: 32 bytes per 243 cells),
+ * so one array holds the sweep (111.6 GB at n = 25 instead of 217.5 GB; the
+ * paper's single in-place array, Table 1), and the bitmap stays there until
+ * the workspace is used again.  Any other overlap with d_work is DQMC_EINVAL.
  * d_count: one uint64, receives the number of primes (may be NULL). */
 int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc,
                     void *d_bitmap, uint64_t *d_count,
@@ -178,7 +225,10 @@ int dqmc_list_dev_ex(uint32_t n, const void *d_on, const void *d_dc,
  * bitmap pass waiting for its tile's bulk copies, or the list's look-back
  * waiting for the tiles before it) gave up after one second; DQMC_ECUDA when
  * a kernel found an index out of bounds and skipped the access.  In both
- * error cases the outputs are not valid.  Device waits never spin
+ * error cases the outputs are not valid: once the error word is set, the
+ * bitmap pass's tiles leave without loading or writing anything (a tile whose
+ * copies did not land waits a second bounded time for them before it leaves).
+ * The next sweep on the workspace clears the word.  Device waits never spin
  * unbounded. */
 int dqmc_dev_status(uint32_t n, const void *d_work, uint64_t work_bytes, void *stream);
 

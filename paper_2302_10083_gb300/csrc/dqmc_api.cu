@@ -433,6 +433,11 @@ static int sweep_dev(uint32_t n, int first, int last, const void *d_on, const vo
     if (first < 0 || first >= last || last > np) return DQMC_EINVAL;
     const Workspace w = workspace_layout((int)n);
     char *base = static_cast<char *>(d_work);
+    // The bitmap may be written over the state (d_bitmap == d_work, n >= 13);
+    // any other overlap of the bitmap with the workspace is refused.
+    const char *bm = static_cast<const char *>(d_bitmap);
+    const bool inplace = !plan.sps.empty() && bm == base + w.state_off;
+    if (!inplace && bm < base + work_bytes && base < bm + bitmap_alloc_bytes((int)n)) return DQMC_EINVAL;
     unsigned long long *cnt = d_count ? reinterpret_cast<unsigned long long *>(d_count)
                                       : reinterpret_cast<unsigned long long *>(base + w.count_off);
     if (plan.sps.empty())
@@ -440,7 +445,7 @@ static int sweep_dev(uint32_t n, int first, int last, const void *d_on, const vo
                                      cnt, static_cast<cudaStream_t>(stream), first, last, nullptr, inv));
     return map_cuda(launch_super(plan, d_on, d_dc, base + w.state_off, static_cast<uint32_t *>(d_bitmap), cnt,
                                  d_pairs, cap, base + w.ctrl_off, static_cast<cudaStream_t>(stream), first, last,
-                                 nullptr, inv));
+                                 nullptr, inv, inplace));
 }
 
 extern "C" int dqmc_primes_dev(uint32_t n, const void *d_on, const void *d_dc, void *d_bitmap,
@@ -564,10 +569,20 @@ static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, 
     const uint64_t tt = ((1ull << n) + 7) / 8;
     const uint64_t tt_alloc = align_up(tt, 16);
     const Workspace w = workspace_layout((int)n);
+    // n = DQMC_MAX_N: the bitmap is written over the state (one array of
+    // 111.6 GB instead of 217.5 GB); smaller n keep a bitmap buffer of their own.
+    const bool inplace = n >= (uint32_t)DQMC_MAX_N && !make_plan((int)n).sps.empty();
     if ((st = ensure(c, 0, tt_alloc))) return st;
     if (dc_bits && (st = ensure(c, 1, tt_alloc))) return st;
-    if ((st = ensure(c, 2, bitmap_alloc_bytes((int)n)))) return st;
+    if (inplace) {
+        if (c->buf[2]) cudaFree(c->buf[2]);   // a bitmap buffer left by a smaller n
+        c->buf[2] = nullptr;
+        c->cap[2] = 0;
+    } else if ((st = ensure(c, 2, bitmap_alloc_bytes((int)n)))) {
+        return st;
+    }
     if ((st = ensure(c, 3, w.total))) return st;
+    void *d_bitmap = inplace ? static_cast<char *>(c->buf[3]) + w.state_off : c->buf[2];
     // A list buffer in pinned host memory that the device can address (8-byte
     // aligned) is written by the kernels directly (over NVLink-C2C on a
     // Grace-based node), so the list needs no copy after the sweep; any other
@@ -592,15 +607,15 @@ static int host_run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, 
     if (e != cudaSuccess) return map_cuda(e);
     uint64_t *dcount = reinterpret_cast<uint64_t *>(c->d_count);
     if (want_list)
-        st = dqmc_list_dev_ex(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, flags, c->buf[2], d_pairs, cap, dcount,
+        st = dqmc_list_dev_ex(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, flags, d_bitmap, d_pairs, cap, dcount,
                               c->buf[3], c->cap[3], s);
     else
-        st = dqmc_primes_dev_ex(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, flags, c->buf[2], dcount, c->buf[3],
+        st = dqmc_primes_dev_ex(n, c->buf[0], dc_bits ? c->buf[1] : nullptr, flags, d_bitmap, dcount, c->buf[3],
                                 c->cap[3], s);
     if (st) return st;
     e = cudaMemcpyAsync(c->h_count, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && out_bitmap)
-        e = cudaMemcpyAsync(out_bitmap, c->buf[2], dqmc_bitmap_bytes(n), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(out_bitmap, d_bitmap, dqmc_bitmap_bytes(n), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return map_cuda(e);
     if ((st = dqmc_dev_status(n, c->buf[3], c->cap[3], s))) return st;

@@ -176,7 +176,7 @@ constexpr uint32_t kErrBounds = 0x424f554eu;   // "BOUN"
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state,
                          uint32_t *d_bitmap, unsigned long long *d_count, uint32_t *d_pairs,
                          uint64_t cap, void *d_ctrl, cudaStream_t stream, int first, int last,
-                         const BatchArgs *batch = nullptr, uint32_t tt_invert = 0);
+                         const BatchArgs *batch = nullptr, uint32_t tt_invert = 0, bool inplace = false);
 
 // Test hook: a device wait on a counter nothing sets; it must time out.
 cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wait_ns, cudaStream_t stream);

@@ -123,6 +123,14 @@ struct PassParams {
     // bitmap pass: the first nbr_k fixed digits (high digits 7 .. 6+nbr_k) are
     // reduced against the '*' neighbour tiles read from the state (0: none)
     int nbr_k;
+    // bitmap pass: the bitmap is written over the state (out == state).  A
+    // tile's bitmap lies at or before its own rows (bit 243 r of the bitmap
+    // for row r at byte 32 r of the state), so it only overwrites rows of
+    // itself and of tiles before it; those tiles, and the tiles before them
+    // that read their rows as '*' neighbours, have all read them once they
+    // have published their counts.  So each tile waits for its look-back
+    // before it writes a bitmap word.
+    int inplace;
     FixedDigits fix;            // digits fixed per tile, ascending
     // Batch mode (bfn non-null): block b works on tile b % tiles_per_fn of
     // function bfn[b / tiles_per_fn]; its truth tables, bitmap and count come
@@ -363,18 +371,20 @@ struct PassShared {
     uint16_t code[kUnits];                // copy of the unit-digit table
 };
 
-// Tile id -> first state row (S.base), first truth-table word (S.ttb) and
-// the literal / value bits of the digits fixed per tile (S.tile_mask / val,
-// bit 5 + j for high digit j).  Thread 0 only, reading the fixed-digit table
-// from the kernel parameters; the caller's next barrier publishes S.  With
-// kTicket and a list, tiles take ids in the order they start, so a tile's
-// look-back waits only on tiles already running.
-template <bool kTicket>
-__device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S, uint64_t tile)
+// A decoded tile: its first state row, its first truth-table word, the
+// literal / value bits of the digits fixed per tile (bit 5 + j for high digit
+// j) and, for the bitmap pass, its '*' neighbour tiles in the neighbour group.
+struct TileInfo {
+    uint64_t base, ttb, tile;
+    uint32_t mask, val;
+    uint32_t nbr_off[kMaxNbr];      // uint4 offsets from the tile's first row
+    int n_nbr;
+};
+
+// Tile id t -> TileInfo, from the fixed-digit table in the kernel parameters.
+__device__ __forceinline__ void decode_tile(const PassParams &P, uint64_t t, TileInfo &T)
 {
     const FixedDigits &f = P.fix;
-    uint64_t t = tile;
-    if (kTicket && P.pairs) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
     uint64_t base = 0, ttb = 0;
     uint32_t m = 0, vv = 0;
     uint32_t dlo = 0;   // 2 bits per digit: values of the first kMaxNbr fixed digits
@@ -414,11 +424,11 @@ __device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S,
             put(i, d);
         }
     }
-    S.base = base;
-    S.ttb = ttb;
-    S.tile = t;
-    S.tile_mask = m;
-    S.tile_val = vv;
+    T.base = base;
+    T.ttb = ttb;
+    T.tile = t;
+    T.mask = m;
+    T.val = vv;
     // The '*' neighbour of this tile in each neighbour-group digit that is
     // 0/1 here: the tile with that digit set to '*', (2 - d) 3^j rows on.
     int nn = 0;
@@ -427,9 +437,29 @@ __device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S,
         if (d == 2) continue;
         const uint64_t off = (uint64_t)(2 - d) * f.w3[i];
         if (ck(P, base + off + kTileRows <= P.state_rows && 2 * off < (1ull << 32), base + off))
-            S.nbr_off[nn++] = (uint32_t)(2 * off);
+            T.nbr_off[nn++] = (uint32_t)(2 * off);
     }
-    S.n_nbr = nn;
+    T.n_nbr = nn;
+}
+
+// Tile id -> PassShared (S.base, S.ttb, S.tile_mask / val, the neighbours).
+// Thread 0 only; the caller's next barrier publishes S.  With kTicket and a
+// list, tiles take ids in the order they start, so a tile's look-back waits
+// only on tiles already running.
+template <bool kTicket>
+__device__ __forceinline__ void decode_tile0(const PassParams &P, PassShared &S, uint64_t tile)
+{
+    uint64_t t = tile;
+    if (kTicket && (P.pairs || P.inplace)) t = atomicAdd(P.ctrl + 1 + P.slot, 1u);
+    TileInfo T;
+    decode_tile(P, t, T);
+    S.base = T.base;
+    S.ttb = T.ttb;
+    S.tile = T.tile;
+    S.tile_mask = T.mask;
+    S.tile_val = T.val;
+    for (int i = 0; i < T.n_nbr; ++i) S.nbr_off[i] = T.nbr_off[i];
+    S.n_nbr = T.n_nbr;
 }
 
 // ------------------------------------------------------------ first pass
@@ -579,22 +609,36 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
         if constexpr (B == 0) {
             // The bitmap pass's tile is one contiguous block of the state (and
             // of shared memory): thread 0 starts its copy (six TMA bulk copies)
-            // at once, before the first barrier.  A tile past the state is
-            // reported and not loaded; the bounded wait below then gives up.
+            // at once, before the first barrier.
             S.load_fail = 0;
             mbar_init(&S.bar, 1);
-            mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
-            constexpr uint32_t kPart = (uint32_t)(kTileRows * kChunkBytes / 6);
-            static_assert(kTileRows * kChunkBytes % 6 == 0 && kPart % 16 == 0, "16-byte multiples");
-            const uint64_t last = S.base + kTileRows - 1;
-            if (ck(P, last < P.state_rows, last)) {
-                const char *src = reinterpret_cast<const char *>(&F.state[2 * S.base]);
-                for (int q = 0; q < 6; ++q)
-                    bulk_g2s(reinterpret_cast<char *>(tile) + q * kPart, src + q * kPart, kPart, &S.bar);
+            if (*reinterpret_cast<volatile uint32_t *>(P.ctrl) != 0u) {
+                // An earlier tile gave up (or found a bad index): the sweep's
+                // outputs are already invalid, so this tile issues no copies
+                // and sweeps nothing.
+                S.load_fail = 2;
+            } else {
+                constexpr uint32_t kPart = (uint32_t)(kTileRows * kChunkBytes / 6);
+                static_assert(kTileRows * kChunkBytes % 6 == 0 && kPart % 16 == 0, "16-byte multiples");
+                const uint64_t last = S.base + kTileRows - 1;
+                if (ck(P, last < P.state_rows, last)) {
+                    mbar_expect_tx(&S.bar, (uint32_t)kUnits * 96u);
+                    const char *src = reinterpret_cast<const char *>(&F.state[2 * S.base]);
+                    for (int q = 0; q < 6; ++q)
+                        bulk_g2s(reinterpret_cast<char *>(tile) + q * kPart, src + q * kPart, kPart, &S.bar);
+                } else {
+                    S.load_fail = 2;   // a tile past the state (reported): not loaded, not swept
+                }
             }
         }
     }
     __syncthreads();
+    if constexpr (B == 0) {
+        if (S.load_fail == 2) {   // nothing in flight: leave at once
+            if (tid == 0) mbar_inval(&S.bar);
+            return;
+        }
+    }
     // the unit tables are copied while the tile's loads are in flight (below)
     auto fill_tables = [&]() {
         for (int i = tid; i < kUnits; i += NT) S.code[i] = g_tab.code[i];
@@ -634,7 +678,11 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
         }
         __syncthreads();
         if (S.load_fail) {
-            // give copies still in flight a bounded time to land, then leave
+            // Give copies still in flight a bounded time to land, then leave.
+            // Every later tile sees the error word before it issues copies of
+            // its own and leaves without touching shared memory, so a copy
+            // that lands after this CTA is gone can only reach shared memory
+            // no tile of this sweep reads.
             if (tid == 0) {
                 const uint64_t t1 = globaltimer_p();
                 while (!mbar_try_wait(&S.bar, 0) && globaltimer_p() - t1 < P.wait_ns) {
@@ -773,7 +821,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
 #pragma unroll
             for (int w = 0; w < NT / 32; ++w) tile_total += S.warp_tot[w];
             if (tid == 0 && tile_total) atomicAdd(F.count, (unsigned long long)tile_total);
-            if (P.pairs && wid == 0) {
+            if ((P.pairs || P.inplace) && wid == 0) {
                 const uint64_t T = S.tile;
                 bool ok = true;
                 unsigned long long ex = 0;
@@ -790,6 +838,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                     S.list_ok = ok;
                 }
             }
+            if (P.inplace) __syncthreads();   // no bitmap word before the look-back
             constexpr int kRegions = (kUnits + 31) / 32;
             for (;;) {
                 int r = 0;
@@ -1024,25 +1073,18 @@ cudaError_t launch_selftest_wait(void *d_ctrl, uint64_t ctrl_bytes, uint64_t wai
 // Threads per CTA and digits per step (measured at n = 24: the last Merge
 // pass 14.70 ms with 384 threads and 2 digits, 14.81 with 384 and 3; the
 // middle Reduce pass 14.78 ms with 256 and 2, 17.26 with 384 and 3).
-// A wide tile (HL = K + B = 8 tile digits, 3^8 rows, 210 KB: one CTA per SM
-// with 1024 threads) carries two inner digits, so its rows go out in runs of
-// nine (288 bytes) instead of three.
-template <bool MERGE, int HL = kTileDigits>
-constexpr int mr_threads() { return HL > kTileDigits ? 1024 : (MERGE ? 384 : 256); }
-template <int HL> constexpr int mr_blocks() { return HL > kTileDigits ? 1 : 3; }
+template <bool MERGE> constexpr int mr_threads() { return MERGE ? 384 : 256; }
 constexpr int kMrDigits = 2;
 
 template <int K, int B, int CM, bool STAGE, bool MERGE>
-__global__ void __launch_bounds__(mr_threads<MERGE, K + B>(), mr_blocks<K + B>())
-    mr_pass_kernel(const __grid_constant__ PassParams P)
+__global__ void __launch_bounds__(mr_threads<MERGE>(), 3) mr_pass_kernel(const __grid_constant__ PassParams P)
 {
     constexpr int HL = K + B;           // tile digits
-    constexpr int NT = mr_threads<MERGE, HL>();
-    constexpr int R = (int)pow3(HL);
+    constexpr int NT = mr_threads<MERGE>();
+    constexpr int R = kTileRows;
     constexpr int RE = (int)pow3(B);   // inner rows per group-digit value
     constexpr int NB = 1 << K;
-    static_assert((HL == kTileDigits || HL == kTileDigits + 1) && B >= 1,
-                  "tiles are 3^7 or 3^8 rows with at least one inner digit");
+    static_assert(HL == kTileDigits && B >= 1, "tiles are 3^7 rows with at least one inner digit");
     extern __shared__ uint4 tile[];
     __shared__ PassShared S;
     const int tid = threadIdx.x;
@@ -1135,12 +1177,12 @@ static cudaError_t launch_unit(const PassParams &p, uint64_t tiles, cudaStream_t
                         unit_threads<MODE>());
 }
 
-template <int K, int CM, bool MERGE, int HL = kTileDigits>
+template <int K, int CM, bool MERGE>
 static cudaError_t launch_mr(const PassParams &p, uint64_t tiles, cudaStream_t stream)
 {
-    constexpr int B = HL - K;
-    const size_t smem = (size_t)pow3(HL) * kChunkBytes;
-    constexpr int NT = mr_threads<MERGE, HL>();
+    constexpr int B = kTileDigits - K;
+    const size_t smem = (size_t)kTileRows * kChunkBytes;
+    constexpr int NT = mr_threads<MERGE>();
     if (p.w_g * kChunkBytes >= kStageStrideBytes)
         return launch_tiles(mr_pass_kernel<K, B, CM, true, MERGE>, smem, p, tiles, stream, NT);
     return launch_tiles(mr_pass_kernel<K, B, CM, false, MERGE>, smem, p, tiles, stream, NT);
@@ -1176,7 +1218,8 @@ static cudaError_t dispatch_group(int K, const PassParams &p, uint64_t tiles, cu
 
 cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, void *d_state, uint32_t *d_bitmap,
                          unsigned long long *d_count, uint32_t *d_pairs, uint64_t cap, void *d_ctrl,
-                         cudaStream_t stream, int first, int last, const BatchArgs *batch, uint32_t tt_invert)
+                         cudaStream_t stream, int first, int last, const BatchArgs *batch, uint32_t tt_invert,
+                         bool inplace)
 {
     const CtrlLayout cl = ctrl_layout(plan);
     cudaError_t e = cudaSuccess;
@@ -1209,6 +1252,7 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
     a.out_alloc_words = bitmap_alloc_bytes(plan.n) / 4;
     a.wait_ns = 1000000000ull;
     a.nmask = (uint32_t)((1ull << plan.n) - 1);
+    a.inplace = (inplace && !batch) ? 1 : 0;
     a.H = plan.H;
     if (batch) {
         a.bfn = batch->fn;
@@ -1242,10 +1286,6 @@ cudaError_t launch_super(const Plan &plan, const void *d_on, const void *d_dc, v
             e = launch_unit<kTileDigits, 0, kLoadFull, kModeOut, 0x1f>(a, tiles, stream);
         else if (ph.out)
             e = cudaErrorInvalidValue;
-        else if (ph.merge && ph.reduce && ph.chunk_mask == 0 && ph.K + ph.B == kTileDigits + 1)
-            e = (ph.K == 6) ? launch_mr<6, 0, true, kTileDigits + 1>(a, tiles, stream) : cudaErrorInvalidValue;
-        else if (ph.K + ph.B != kTileDigits)
-            e = cudaErrorInvalidValue;      // wide tiles: only the last Merge pass of six digits
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0)
             e = dispatch_mr<0, true>(ph.K, a, tiles, stream);
         else if (ph.merge && ph.reduce && ph.chunk_mask == 0x07)

@@ -110,6 +110,16 @@ __device__ __forceinline__ void reduce_step(uint4 *S, int lt, int tg)
             constexpr int t = decltype(Ti)::value;
             x[t] = bp[4 * t * P];
         });
+        {
+            // Only a set cell of a row with a '*' in these digits clears
+            // anything: with none set, the block stays as it is.
+            uint32_t src = 0;
+            static_for<0, T>([&](auto Ti) {
+                constexpr int t = decltype(Ti)::value;
+                if constexpr (twos_of(t, DD) > 0) src |= x[t].x | x[t].y;
+            });
+            if (src == 0) continue;
+        }
         static_for<0, DD>([&](auto Ki) {
             constexpr int k = decltype(Ki)::value;   // number of '*' digits of the rows updated now
             static_for<0, T>([&](auto Ti) {

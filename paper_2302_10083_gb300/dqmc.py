@@ -58,6 +58,9 @@ _SIGS = {
                                           ctypes.c_uint64, c_vp]),
     "dqmc_list_dev_ex": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, ctypes.c_uint32, c_vp, c_vp, ctypes.c_uint64,
                                         c_vp, c_vp, ctypes.c_uint64, c_vp]),
+    "dqmc_sparse_list": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, ctypes.c_uint32, c_u32p, ctypes.c_uint64,
+                                        c_u64p]),
+    "dqmc_cover": (ctypes.c_int, [ctypes.c_uint32, c_u8p, c_u8p, c_u32p, ctypes.c_uint64, c_u32p, c_u64p]),
     "dqmc_release": (None, []),
     "dqmc_primes_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp]),
     "dqmc_list_dev": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, c_vp, c_vp,
@@ -253,6 +256,42 @@ def dqmc_list_ex(n: int, on_bits, dc_bits=None, flags: int = 0, cap: int = 0):
     return out[: 2 * k].reshape(k, 2), int(c.value)
 
 
+DQMC_SPARSE_MAX_N = 30
+
+
+def dqmc_sparse_list(n: int, on_bits, dc_bits=None, flags: int = 0, cap: int | None = None):
+    """(pairs (k, 2) uint32 in ascending rho, count) through dqmc_sparse_list
+    (SparseQMC on the GPU); cap=None sizes the buffer as dqmc_list does."""
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    auto = cap is None
+    if auto:
+        cap = _list_cap_guess(n, on, dc)
+    while True:
+        out = np.empty(2 * max(cap, 1), dtype=np.uint32)
+        c = ctypes.c_uint64()
+        st = lib().dqmc_sparse_list(n, _p8(on), _p8(dc), flags, out.ctypes.data_as(c_u32p), cap, ctypes.byref(c))
+        _check(st, "dqmc_sparse_list", ok=(DQMC_OK, DQMC_ETRUNC))
+        if not (auto and st == DQMC_ETRUNC):
+            break
+        cap = int(c.value)
+    k = min(int(c.value), cap)
+    return out[: 2 * k].reshape(k, 2), int(c.value)
+
+
+def dqmc_cover(n: int, on_bits, dc_bits, pairs) -> np.ndarray:
+    """Indexes (ascending) of the primes dqmc_cover selects: essentials, then
+    greedy by uncovered ON minterms (ties: lowest index)."""
+    on = _host_tt(on_bits, n)
+    dc = _host_tt(dc_bits, n)
+    pr = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty(max(len(pr), 1), dtype=np.uint32)
+    k = ctypes.c_uint64()
+    _check(lib().dqmc_cover(n, _p8(on), _p8(dc), pr.ctypes.data_as(c_u32p), len(pr), out.ctypes.data_as(c_u32p),
+                            ctypes.byref(k)), "dqmc_cover")
+    return out[: k.value].copy()
+
+
 def dqmc_release() -> None:
     lib().dqmc_release()
 
@@ -306,20 +345,27 @@ def dqmc_compact_dev(n, d_bitmap, d_pairs, cap, d_count, d_work, work_bytes, str
 # ------------------------------------------------------- torch conveniences
 
 class DeviceBuffers:
-    """Device tensors for one n: inputs, bitmap, count, workspace (torch-owned)."""
+    """Device tensors for one n: inputs, bitmap, count, workspace (torch-owned).
+    With inplace=True (n >= 13) the bitmap is the start of the workspace: the
+    sweep writes it over its state (one array instead of two)."""
 
-    def __init__(self, n: int, device="cuda", with_dc: bool = False, cap: int = 0):
+    def __init__(self, n: int, device="cuda", with_dc: bool = False, cap: int = 0, inplace: bool = False):
         import torch
         self.n = n
         tt = max(((1 << n) + 7) >> 3, 1)
         tt_alloc = (tt + 15) // 16 * 16
         self.on = torch.zeros(tt_alloc, dtype=torch.uint8, device=device)
         self.dc = torch.zeros(tt_alloc, dtype=torch.uint8, device=device) if with_dc else None
-        self.bitmap = torch.empty(dqmc_bitmap_alloc_bytes(n), dtype=torch.uint8, device=device)
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
         wb = dqmc_workspace_bytes(n)
         self.work = torch.empty(max(wb, 256), dtype=torch.uint8, device=device)
         self.work_bytes = self.work.numel()
+        if inplace:
+            if n < 13:
+                raise ValueError("the bitmap can share the workspace only for n >= 13")
+            self.bitmap = self.work[: dqmc_bitmap_alloc_bytes(n)]
+        else:
+            self.bitmap = torch.empty(dqmc_bitmap_alloc_bytes(n), dtype=torch.uint8, device=device)
         self.cap = cap
         self.pairs = torch.empty(2 * max(cap, 1), dtype=torch.int32, device=device)
 

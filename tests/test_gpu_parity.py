@@ -267,6 +267,41 @@ def test_bounded_wait_times_out_and_context_survives():
     assert np.array_equal(buf.bitmap[: (3 ** n + 7) // 8].cpu().numpy(), oracle.bitmap(n, S))
 
 
+@pytest.mark.parametrize("with_list", [False, True])
+def test_bitmap_pass_after_a_timeout_sweeps_nothing(with_list):
+    """The bitmap pass's error path, driven without a fault: after a bounded
+    wait has given up (the self test leaves DQMC_ETIMEOUT in the error word),
+    every tile of a bitmap pass on that workspace sees the error word before
+    it issues its bulk copies and leaves without sweeping, so the bitmap keeps
+    its old contents, the status stays DQMC_ETIMEOUT, and the next whole sweep
+    on the same workspace is bit-exact."""
+    n = 16
+    on, _ = synth.random_function(n, 5, 0.8)
+    buf = dqmc.DeviceBuffers(n, cap=1 << 20)
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    sh = torch.cuda.current_stream().cuda_stream
+    last = dqmc.dqmc_plan_passes(n) - 1
+    cap = buf.cap if with_list else 0
+    pairs = buf.pairs.data_ptr() if with_list else None
+    L = dqmc.lib()
+    assert L.dqmc_sweep_passes_dev(n, 0, last, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), pairs, cap,
+                                   buf.count.data_ptr(), buf.work.data_ptr(), buf.work_bytes, sh) == dqmc.DQMC_OK
+    torch.cuda.synchronize()
+    dqmc.dqmc_selftest_timeout(n, buf.work.data_ptr(), buf.work_bytes, 1_000_000, sh)
+    buf.bitmap.fill_(0xA5)
+    assert L.dqmc_sweep_pass_dev(n, last, buf.on.data_ptr(), None, buf.bitmap.data_ptr(), pairs, cap,
+                                 buf.count.data_ptr(), buf.work.data_ptr(), buf.work_bytes, sh) == dqmc.DQMC_OK
+    with pytest.raises(dqmc.DqmcError) as ei:
+        buf.status()
+    assert ei.value.status == dqmc.DQMC_ETIMEOUT
+    assert bool((buf.bitmap == 0xA5).all())
+    buf.list()
+    buf.status()
+    S = oracle.sweep(n, on)
+    assert np.array_equal(buf.bitmap[: (3 ** n + 7) // 8].cpu().numpy(), oracle.bitmap(n, S))
+    assert int(buf.count.item()) == oracle.count(n, S)
+
+
 # ------------------------------------------------------ large n, sampled
 
 def _sample_bits(bitmap_dev, rhos):
@@ -275,14 +310,15 @@ def _sample_bits(bitmap_dev, rhos):
     return ((bytes_ >> (rhos & 7).astype(np.uint8)) & 1).astype(bool)
 
 
-def sampled_check(n, on, dc, p_support, n_list=20000, n_cells=200000, seed=24):
+def sampled_check(n, on, dc, p_support, n_list=20000, n_cells=200000, seed=24, inplace=False):
     """Sweep + list in the benchmark's launch configuration (device API), then:
     every sampled listed prime is prime by definition and set in the bitmap, the
     list is ascending, sampled cells agree with the pointwise oracle, the two
-    independent counts agree, and the count is within 1% of its expectation."""
+    independent counts agree, and the count is within 1% of its expectation.
+    inplace: the bitmap is written over the state (one array)."""
     expected = bf.expected_primes(n, p_support)
     cap = int(expected * 1.05) + 4096
-    buf = dqmc.DeviceBuffers(n, with_dc=dc is not None, cap=cap)
+    buf = dqmc.DeviceBuffers(n, with_dc=dc is not None, cap=cap, inplace=inplace)
     buf.on[: on.size].copy_(torch.from_numpy(on))
     if dc is not None:
         buf.dc[: dc.size].copy_(torch.from_numpy(dc))
@@ -332,14 +368,48 @@ def test_n24_workload_sampled():
 
 
 def test_n25_stretch_sampled():
-    """n = 25, ON ~ Bernoulli(0.85), seed 1: the largest size (state 111.6 GB +
-    bitmap 105.9 GB in device memory), sampled as at n = 24."""
+    """n = 25, ON ~ Bernoulli(0.85), seed 1: the largest size, in one array
+    (the bitmap written over the 111.6 GB state, as the paper's in-place
+    array of Table 1), sampled as at n = 24."""
     free, _ = torch.cuda.mem_get_info()
-    need = dqmc.dqmc_workspace_bytes(25) + dqmc.dqmc_bitmap_alloc_bytes(25) + int(1.1e9) * 8
+    need = dqmc.dqmc_workspace_bytes(25) + int(1.1e9) * 8
     if free < need:
         pytest.skip(f"needs {need / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
     on, _ = synth.random_function(25, 1, 0.85)
-    sampled_check(25, on, None, 0.85, n_list=5000, n_cells=50000)
+    sampled_check(25, on, None, 0.85, n_list=5000, n_cells=50000, inplace=True)
+
+
+@pytest.mark.parametrize("n,with_list", [(13, True), (16, False), (16, True), (19, True)])
+def test_inplace_bitmap_exact(n, with_list):
+    """The bitmap written over the state (d_bitmap = d_work): bit-exact
+    against the oracle, with and without the list."""
+    on, dc = synth.random_function(n, 60 + n, 0.8, 0.05)
+    S = oracle.sweep(n, on, dc)
+    want_bm, want_pairs = oracle.bitmap(n, S), oracle.pairs(n, S)
+    buf = dqmc.DeviceBuffers(n, with_dc=True, cap=len(want_pairs) if with_list else 0, inplace=True)
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    buf.dc[: dc.size].copy_(torch.from_numpy(dc))
+    if with_list:
+        buf.list()
+    else:
+        buf.primes()
+    buf.status()
+    assert int(buf.count.item()) == len(want_pairs)
+    assert np.array_equal(buf.bitmap[: want_bm.size].cpu().numpy(), want_bm)
+    if with_list:
+        got = buf.pairs[: 2 * len(want_pairs)].cpu().numpy().view(np.uint32).reshape(-1, 2)
+        assert np.array_equal(got, want_pairs)
+
+
+def test_inplace_bitmap_overlap_refused():
+    """Any overlap of the bitmap with the workspace other than the in-place
+    start is refused before any work is enqueued."""
+    n = 14
+    buf = dqmc.DeviceBuffers(n, inplace=True)
+    L = dqmc.lib()
+    st = L.dqmc_primes_dev(n, buf.on.data_ptr(), None, buf.work.data_ptr() + 256, buf.count.data_ptr(),
+                           buf.work.data_ptr(), buf.work_bytes, None)
+    assert st == dqmc.DQMC_EINVAL
 
 
 @pytest.mark.parametrize("n", [11, 17, 20])

@@ -91,3 +91,31 @@ def test_bitmap_list_digests_and_count(n):
     pairs, c = dqmc.dqmc_list(n, on, dc, cap=count)
     assert c == count and pairs.shape == (count, 2)
     assert hashlib.sha256(memoryview(np.ascontiguousarray(pairs, dtype="<u4"))).hexdigest() == want_list
+
+
+@pytest.mark.parametrize("n", [22, 23])
+def test_inplace_bitmap_digests(n):
+    """The bitmap written over the state (d_bitmap = d_work, one array): the
+    same SHA-256 of the bitmap and the list as the oracle's."""
+    if n not in CASES:
+        pytest.skip(f"no stored digest for n = {n}")
+    seed, p_on, p_dc, count, want, want_list = CASES[n]
+    A = (3 ** n + 7) // 8
+    if _mem_available_bytes() < A + (4 << 30):
+        pytest.skip(f"needs about {(A >> 30) + 4} GiB of available host memory")
+    on, dc = synth.random_function(n, seed, p_on, p_dc)
+    buf = dqmc.DeviceBuffers(n, with_dc=dc is not None, cap=count, inplace=True)
+    assert buf.bitmap.data_ptr() == buf.work.data_ptr()
+    buf.on[: on.size].copy_(torch.from_numpy(on))
+    if dc is not None:
+        buf.dc[: dc.size].copy_(torch.from_numpy(dc))
+    buf.list()
+    buf.status()
+    assert int(buf.count.item()) == count
+    got = buf.bitmap[:A].cpu().numpy()
+    assert hashlib.sha256(memoryview(got)).hexdigest() == want
+    del got
+    pairs = buf.pairs[: 2 * count].cpu().numpy().view(np.uint32)
+    assert hashlib.sha256(memoryview(np.ascontiguousarray(pairs, dtype="<u4"))).hexdigest() == want_list
+    del buf
+    torch.cuda.empty_cache()
