@@ -887,7 +887,9 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                     const uint32_t s0 = lb0 & 31;
                     uint32_t *const uw = stg + (lb0 >> 5);
                     uint32_t carry = 0, first = 0;
-                    if (valid) {
+                    // a region with no set cell writes zero words and stages nothing
+                    const bool empty = (wtot == 0u);
+                    if (valid && !empty) {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
                             const uint32_t sb = s0 + 243u * (uint32_t)k;  // row k's first bit, from uw
@@ -909,7 +911,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                         }
                     }
                     const uint32_t cin = __shfl_up_sync(0xffffffffu, carry, 1);
-                    if (valid) {
+                    if (valid && !empty) {
                         uw[0] = first | (lane > 0 ? cin : 0u);
                         if (lane == nun - 1) uw[(s0 + 729u) >> 5] = carry;  // the region's last word
                     }
@@ -920,20 +922,27 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                         // 32 full units: words 1 .. 728 hold only their bits;
                         // word 0 holds them from bit o up, word 729 below bit o.
                         uint32_t *const dstw = out + S0;
+                        if (empty) {
 #pragma unroll 4
-                        for (int j = 1 + lane; j <= 728; j += 32) dstw[j] = stg[j];
+                            for (int j = 1 + lane; j <= 728; j += 32) dstw[j] = 0u;
+                        } else {
+#pragma unroll 4
+                            for (int j = 1 + lane; j <= 728; j += 32) dstw[j] = stg[j];
+                        }
                         if (lane == 0) {
+                            const uint32_t v0 = empty ? 0u : stg[0];
                             if (o == 0) {
-                                dstw[0] = stg[0];
+                                dstw[0] = v0;
                             } else {
                                 const uint32_t m = 0xffffffffu << o;
-                                atomicAnd(dstw, stg[0] | ~m);
-                                atomicOr(dstw, stg[0] & m);
+                                atomicAnd(dstw, v0 | ~m);
+                                atomicOr(dstw, v0 & m);
                             }
                         } else if (lane == 1 && o != 0) {
                             const uint32_t m = (1u << o) - 1u;
-                            atomicAnd(dstw + 729, stg[729] | ~m);
-                            atomicOr(dstw + 729, stg[729] & m);
+                            const uint32_t v1 = empty ? 0u : stg[729];
+                            atomicAnd(dstw + 729, v1 | ~m);
+                            atomicOr(dstw + 729, v1 & m);
                         }
                     } else {
                         const int nw = (int)((hi_bit + 31u) >> 5);
@@ -945,7 +954,7 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                             const int hi2 = (last_tile && wi == P.out_words - 1) ? 32 : hi;  // bits past 3^n are 0
                             if (hi2 <= lo) continue;
                             if (!ck(P, wi < P.out_alloc_words, wi)) continue;
-                            const uint32_t val = stg[j];
+                            const uint32_t val = empty ? 0u : stg[j];
                             uint32_t *dst = out + wi;
                             if (lo == 0 && hi2 == 32) {
                                 *dst = val;
