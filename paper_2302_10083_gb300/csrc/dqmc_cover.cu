@@ -10,7 +10,9 @@
 // Don't-care minterms need no cover.  The state is one bit per minterm
 // ("still to cover"); a prime (mask, value) with w wildcards covers the 2^w
 // minterms value | deposit(k, ~mask), k < 2^w, which one warp per prime
-// enumerates (lanes split k).
+// enumerates (lanes split k).  The greedy part runs one level of the maximum
+// count per round (level_kernel), which takes exactly the primes the
+// one-at-a-time rule takes, in the same order.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -77,23 +79,62 @@ __global__ void cover_kernel(const uint2 *pairs, uint64_t np, uint32_t full, con
     }
 }
 
-// the best unselected prime: (uncovered minterms it covers) << 32 | ~index,
-// so the largest value is the most minterms, then the lowest index
-__global__ void best_kernel(const uint2 *pairs, uint64_t np, uint32_t full, const uint8_t *sel,
-                            const uint32_t *todo, unsigned long long *best)
+// uncovered ON minterms of prime p (all lanes of the warp get the sum)
+__device__ __forceinline__ uint32_t warp_count(const uint2 *pairs, uint64_t p, uint32_t full, const uint32_t *todo,
+                                               int lane)
+{
+    const uint2 mv = pairs[p];
+    const uint32_t free_bits = ~mv.x & full;
+    const uint64_t nk = 1ull << __popc(free_bits);
+    uint32_t c = 0;
+    for (uint64_t k = lane; k < nk; k += 32) c += get_bit(todo, cube_minterm(free_bits, mv.y, (uint32_t)k));
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    return c;
+}
+
+// every unselected prime's count of uncovered ON minterms, and their maximum
+__global__ void count_kernel(const uint2 *pairs, uint64_t np, uint32_t full, const uint8_t *sel,
+                             const uint32_t *todo, uint32_t *cnt, unsigned int *best)
 {
     const uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= np) return;
-    uint32_t c = 0;
-    if (!sel[p]) {
-        const uint2 mv = pairs[p];
-        const uint32_t free_bits = ~mv.x & full;
-        const uint64_t nk = 1ull << __popc(free_bits);
-        for (uint64_t k = lane; k < nk; k += 32) c += get_bit(todo, cube_minterm(free_bits, mv.y, (uint32_t)k));
+    const uint32_t c = sel[p] ? 0u : warp_count(pairs, p, full, todo, lane);
+    if (lane == 0) {
+        cnt[p] = c;
+        if (c) atomicMax(best, c);
     }
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    if (lane == 0 && c) atomicMax(best, ((unsigned long long)c << 32) | (uint32_t)~(uint32_t)p);
+}
+
+// One greedy level, by one warp, primes in index order: a prime whose count
+// was the maximum is taken if it still is (then its minterms are covered).
+// Every other prime's count is below the maximum and can only fall, so the
+// lowest-index prime still at the maximum is exactly the prime that taking
+// one prime at a time (most uncovered minterms, lowest index) would take next.
+__global__ void level_kernel(const uint2 *pairs, uint64_t np, uint32_t full, uint8_t *sel, uint32_t *todo,
+                             const uint32_t *cnt, uint32_t best)
+{
+    const int lane = threadIdx.x;
+    for (uint64_t p0 = 0; p0 < np; p0 += 32) {
+        const uint64_t mine = p0 + lane;
+        const bool cand = mine < np && !sel[mine] && cnt[mine] == best;
+        uint32_t m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t p = p0 + l;
+            if (warp_count(pairs, p, full, todo, lane) != best) continue;
+            if (lane == 0) sel[p] = 1;
+            const uint2 mv = pairs[p];
+            const uint32_t free_bits = ~mv.x & full;
+            const uint64_t nk = 1ull << __popc(free_bits);
+            for (uint64_t k = lane; k < nk; k += 32) {
+                const uint32_t t = cube_minterm(free_bits, mv.y, (uint32_t)k);
+                atomicAnd(todo + (t >> 5), ~(1u << (t & 31)));
+            }
+            __syncwarp();
+        }
+    }
 }
 
 static int map_err(cudaError_t e)
@@ -143,13 +184,11 @@ static int run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, const
     uint32_t *d_todo = nullptr, *d_cnt = nullptr, *d_who = nullptr;
     uint2 *d_pairs = nullptr;
     uint8_t *d_sel = nullptr;
-    unsigned long long *d_best = nullptr;
     if ((e = B.alloc((void **)&d_todo, words * 4)) != cudaSuccess) return map_err(e);
     if ((e = B.alloc((void **)&d_cnt, m * 4)) != cudaSuccess) return map_err(e);
     if ((e = B.alloc((void **)&d_who, m * 4)) != cudaSuccess) return map_err(e);
     if ((e = B.alloc((void **)&d_pairs, np * 8)) != cudaSuccess) return map_err(e);
     if ((e = B.alloc((void **)&d_sel, np)) != cudaSuccess) return map_err(e);
-    if ((e = B.alloc((void **)&d_best, 8)) != cudaSuccess) return map_err(e);
     e = cudaMemcpyAsync(d_todo, todo.data(), words * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && np) e = cudaMemcpyAsync(d_pairs, pairs, np * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, m * 4, s);
@@ -162,18 +201,19 @@ static int run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, const
         essential_kernel<<<gm, kThreads, 0, s>>>(d_cnt, d_who, d_todo, m, d_sel);
         cover_kernel<<<gp, kThreads, 0, s>>>(d_pairs, np, full, d_sel, d_todo);
     }
-    // greedy: one prime per round (rounds <= primes)
-    for (uint64_t round = 0; np && round < np; ++round) {
-        if ((e = cudaMemsetAsync(d_best, 0, 8, s)) != cudaSuccess) return map_err(e);
-        best_kernel<<<gp, kThreads, 0, s>>>(d_pairs, np, full, d_sel, d_todo, d_best);
-        unsigned long long h = 0;
-        if ((e = cudaMemcpyAsync(&h, d_best, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return map_err(e);
+    // greedy, one level of the maximum count per round (rounds <= the largest count)
+    uint32_t *d_c = nullptr;
+    unsigned int *d_b = nullptr;
+    if ((e = B.alloc((void **)&d_c, np * 4)) != cudaSuccess) return map_err(e);
+    if ((e = B.alloc((void **)&d_b, 4)) != cudaSuccess) return map_err(e);
+    for (uint64_t round = 0; round < np; ++round) {   // each round takes at least one prime
+        if ((e = cudaMemsetAsync(d_b, 0, 4, s)) != cudaSuccess) return map_err(e);
+        count_kernel<<<gp, kThreads, 0, s>>>(d_pairs, np, full, d_sel, d_todo, d_c, d_b);
+        unsigned int best = 0;
+        if ((e = cudaMemcpyAsync(&best, d_b, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return map_err(e);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_err(e);
-        if (h == 0) break;   // nothing left to cover
-        const uint64_t p = (uint32_t)~(uint32_t)(h & 0xffffffffu);
-        const uint8_t one = 1;
-        if ((e = cudaMemcpyAsync(d_sel + p, &one, 1, cudaMemcpyHostToDevice, s)) != cudaSuccess) return map_err(e);
-        cover_kernel<<<(32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_pairs + p, 1, full, d_sel + p, d_todo);
+        if (best == 0) break;   // nothing left to cover
+        level_kernel<<<1, 32, 0, s>>>(d_pairs, np, full, d_sel, d_todo, d_c, best);
     }
     std::vector<uint8_t> sel(np);
     if (np && (e = cudaMemcpyAsync(sel.data(), d_sel, np, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
