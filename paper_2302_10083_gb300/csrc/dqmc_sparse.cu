@@ -17,7 +17,7 @@
 //             cubes u with '0' and with '1' at j are flagged redundant in
 //             L_{w-1} (the extra pass the rule makes necessary);
 //   collect   the unflagged cubes of L_{w-1} are prime.
-// The primes are then sorted by rho (bitonic sort) and written as (mask,
+// The primes are then sorted by rho (a radix sort) and written as (mask,
 // value) pairs in ascending rho, the order of dqmc_list.
 #include <cstdio>
 #include <cstring>
@@ -186,21 +186,98 @@ __global__ void collect_kernel(const uint64_t *tab, uint64_t slots, int n, uint6
     }
 }
 
-// one compare-exchange step of a bitonic sort of (key, value) pairs
-__global__ void bitonic_kernel(uint64_t *keys, uint64_t *vals, uint64_t len, uint64_t j, uint64_t k)
+// ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (key, value) pairs by 8-bit digits.  A block owns
+// a tile of kSortTile consecutive pairs; its 8 warps own 512 each, taken in
+// rounds of 32.  Per digit pass: each block's digit histogram (digit-major,
+// block-minor in global memory), one exclusive scan of it, then the scatter:
+// a pair's place is its digit's scanned base for the block, plus the counts
+// of that digit in the block's earlier warps, earlier rounds of its warp, and
+// earlier lanes of its round (__match_any_sync), so equal digits keep their
+// order.
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortPerWarp = 512;
+constexpr int kSortTile = kSortWarps * kSortPerWarp;   // 4096
+
+__global__ void hist_kernel(const uint64_t *keys, uint64_t len, int shift, uint32_t *hist, uint32_t nblocks)
 {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= len) return;
-    const uint64_t p = i ^ j;
-    if (p <= i || p >= len) return;
-    const bool up = (i & k) == 0;
-    const uint64_t a = keys[i], b = keys[p];
-    if ((a > b) == up) {
-        keys[i] = b;
-        keys[p] = a;
-        const uint64_t t = vals[i];
-        vals[i] = vals[p];
-        vals[p] = t;
+    __shared__ uint32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
+        const uint64_t k = t0 + i;
+        if (k < len) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(uint64_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+// exclusive scan of cnt in place, by one block of 1024 threads
+__global__ void scan_kernel(uint32_t *cnt, uint64_t n)
+{
+    __shared__ uint32_t part[1024];
+    const uint64_t per = (n + 1023) / 1024;
+    const uint64_t b0 = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (uint64_t i = b0; i < b0 + per && i < n; ++i) sum += cnt[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t y = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (uint64_t i = b0; i < b0 + per && i < n; ++i) {
+        const uint32_t c = cnt[i];
+        cnt[i] = run;
+        run += c;
+    }
+}
+
+__global__ void scatter_kernel(const uint64_t *keys, const uint64_t *vals, uint64_t len, int shift,
+                               const uint32_t *base, uint32_t nblocks, uint64_t *okeys, uint64_t *ovals)
+{
+    __shared__ uint32_t wcnt[kSortWarps][256];   // per warp: its pairs of each digit, then their offsets
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * kSortTile + (uint64_t)w * kSortPerWarp;
+    for (int r = 0; r < kSortPerWarp; r += 32) {
+        const uint64_t k = t0 + r + lane;
+        const bool in = k < len;
+        const uint32_t d = in ? (uint32_t)((keys[k] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
+    }
+    __syncthreads();
+    // offsets: the digit's base for this block, then the earlier warps' counts
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        uint32_t run = base[(uint64_t)d * nblocks + blockIdx.x];
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            const uint32_t c = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < kSortPerWarp; r += 32) {
+        const uint64_t k = t0 + r + lane;
+        const bool in = k < len;
+        const uint64_t key = in ? keys[k] : 0ull;
+        const uint32_t d = in ? (uint32_t)((key >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in) {
+            const uint32_t at = wcnt[w][d] + __popc(peers & ((1u << lane) - 1u));
+            okeys[at] = key;
+            ovals[at] = vals[k];
+        }
+        __syncwarp();
+        if (in && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
+        __syncwarp();
     }
 }
 
@@ -236,6 +313,13 @@ struct Bufs {
 };
 
 static unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+static uint64_t pow3u(uint32_t n)
+{
+    uint64_t p = 1;
+    for (uint32_t i = 0; i < n; ++i) p *= 3u;
+    return p;
+}
 
 static int lg_slots(uint64_t len)
 {
@@ -364,21 +448,28 @@ static int run(uint32_t n, const uint8_t *on_bits, const uint8_t *dc_bits, uint3
         cur = next;
         len = nlen;
     }
-    // ascending rho: bitonic sort over the next power of two (padding keys last)
-    uint64_t N = 1;
-    while (N < np) N <<= 1;
-    if (N > pcap) {
+    // ascending rho: LSD radix sort, 8 bits a pass, over the bits rho can have
+    if (np > 1) {
+        int bits = 1;
+        while (bits < 64 && (1ull << bits) < pow3u(n)) ++bits;
+        const uint32_t nblocks = (uint32_t)((np + kSortTile - 1) / kSortTile);
         uint64_t *k2 = nullptr, *v2 = nullptr;
-        if ((e = B.alloc((void **)&k2, N * 8)) != cudaSuccess) return map_err(e);
-        if ((e = B.alloc((void **)&v2, N * 8)) != cudaSuccess) return map_err(e);
-        if (np && (e = cudaMemcpyAsync(k2, keys, np * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return map_err(e);
-        if (np && (e = cudaMemcpyAsync(v2, vals, np * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return map_err(e);
-        keys = k2;
-        vals = v2;
+        uint32_t *hist = nullptr;
+        if ((e = B.alloc((void **)&k2, np * 8)) != cudaSuccess) return map_err(e);
+        if ((e = B.alloc((void **)&v2, np * 8)) != cudaSuccess) return map_err(e);
+        if ((e = B.alloc((void **)&hist, (uint64_t)nblocks * 256 * 4)) != cudaSuccess) return map_err(e);
+        for (int shift = 0; shift < bits; shift += 8) {
+            hist_kernel<<<nblocks, kSortThreads, 0, s>>>(keys, np, shift, hist, nblocks);
+            scan_kernel<<<1, 1024, 0, s>>>(hist, (uint64_t)nblocks * 256);
+            scatter_kernel<<<nblocks, kSortThreads, 0, s>>>(keys, vals, np, shift, hist, nblocks, k2, v2);
+            uint64_t *t = keys;
+            keys = k2;
+            k2 = t;
+            t = vals;
+            vals = v2;
+            v2 = t;
+        }
     }
-    if (N > np) fill_kernel<<<blocks_for(N - np), kThreads, 0, s>>>(keys + np, N - np, ~0ull);
-    for (uint64_t k = 2; k <= N; k <<= 1)
-        for (uint64_t j = k >> 1; j > 0; j >>= 1) bitonic_kernel<<<blocks_for(N), kThreads, 0, s>>>(keys, vals, N, j, k);
     const uint64_t kout = np < cap ? np : cap;
     if (kout) {
         uint2 *d_pairs = nullptr;

@@ -315,7 +315,8 @@ def sampled_check(n, on, dc, p_support, n_list=20000, n_cells=200000, seed=24, i
     every sampled listed prime is prime by definition and set in the bitmap, the
     list is ascending, sampled cells agree with the pointwise oracle, the two
     independent counts agree, and the count is within 1% of its expectation.
-    inplace: the bitmap is written over the state (one array)."""
+    inplace: the bitmap is written over the state (one array).  Returns the
+    prime count."""
     expected = bf.expected_primes(n, p_support)
     cap = int(expected * 1.05) + 4096
     buf = dqmc.DeviceBuffers(n, with_dc=dc is not None, cap=cap, inplace=inplace)
@@ -352,6 +353,7 @@ def sampled_check(n, on, dc, p_support, n_list=20000, n_cells=200000, seed=24, i
     assert not buf.bitmap[nb:].any().item()
     del buf
     torch.cuda.empty_cache()
+    return count
 
 
 @pytest.mark.parametrize("n", [22, 23])
@@ -376,7 +378,11 @@ def test_n25_stretch_sampled():
     if free < need:
         pytest.skip(f"needs {need / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
     on, _ = synth.random_function(25, 1, 0.85)
-    sampled_check(25, on, None, 0.85, n_list=5000, n_cells=50000, inplace=True)
+    count = sampled_check(25, on, None, 0.85, n_list=5000, n_cells=50000, inplace=True)
+    # the host entry points write the bitmap over the state at n = 25 too
+    dqmc.dqmc_release()
+    assert dqmc.dqmc_count(25, on) == count
+    dqmc.dqmc_release()
 
 
 @pytest.mark.parametrize("n,with_list", [(13, True), (16, False), (16, True), (19, True)])
