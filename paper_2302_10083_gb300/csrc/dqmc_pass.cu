@@ -23,11 +23,18 @@
 //          implicant one-digit extension is cleared in the first group that
 //          holds such a digit (the extension is still set then: clearing it
 //          would need an extension of the cube in an earlier group), and
-//          primes are never cleared;
+//          primes are never cleared.  The bitmap pass also reduces the group
+//          just above its tile (the neighbour group) against the '*'
+//          neighbour tiles, read from the state as the last Merge pass left
+//          it; a block or row with no set cell skips the work that could
+//          only leave it as it is;
 //   store  rows back to the state, or, in the last pass, the dense bitmap
 //          (each warp funnel-shifts its 96 rows into their own, no longer
-//          needed, slots of the tile), the count, and the (mask, value) list
-//          placed by a decoupled look-back over the tiles in rho order.
+//          needed, slots of the tile; a region with no set cell writes zero
+//          words), the count, and the (mask, value) list placed by a
+//          decoupled look-back over the tiles in rho order.  The bitmap may be
+//          written over the state itself (in-place mode): each tile then
+//          waits for its look-back before it writes a bitmap word.
 //
 // Two kernels:
 //   mr_pass_kernel   the last Merge pass and the Reduce passes: the tile
