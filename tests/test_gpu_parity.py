@@ -418,7 +418,7 @@ def test_inplace_bitmap_overlap_refused():
     assert st == dqmc.DQMC_EINVAL
 
 
-@pytest.mark.parametrize("n", [11, 17, 20])
+@pytest.mark.parametrize("n", [11, 17, 20, 22])
 def test_list_into_pinned_host_memory(n):
     """dqmc_list into pinned host memory (written by the kernels directly)
     equals the list through pageable memory (device buffer and a copy), also
