@@ -531,9 +531,33 @@ def run_batched(args, rank, world, local, emit=True):
     bm_graph = bitmaps.clone()
     cnt_graph = counts.clone()
 
+    # the same batch in one persistent launch (dqmc_batch_run_one_launch)
+    def one_run():
+        st = dqmc.dqmc_batch_run(ns, b["tt_off"], arena.data_ptr(), b["dc_off"], counts.data_ptr(),
+                                 bitmaps.data_ptr(), bm_off, sh, one_launch=True)
+        if st != 0:
+            raise dqmc.DqmcError(st, "dqmc_batch_run_one_launch")
+
+    bitmaps.zero_()
+    counts.zero_()
+    for _ in range(max(args.warmup, 1)):
+        one_run()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        one_run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = e0.elapsed_time(e1) / K
+    one = {"value": world * nf / (ms_one / 1e3), "unit": "functions/s", "ms_per_step": ms_one,
+           "api": "dqmc_batch_run_one_launch (one persistent kernel per graph launch)",
+           "results_identical": bool(torch.equal(bm_graph, bitmaps) and torch.equal(cnt_graph, counts))}
+    if not one["results_identical"]:
+        raise SystemExit("one-launch and graph results differ")
+
     if args.no_one_by_one:
         return report_batched(args, rank, world, b, nf, ns, total, ms, clocks, None, None, True, tune_s, tune_ms,
-                              table, None, emit)
+                              table, None, emit, one)
 
     # one launch sequence per function (dqmc_primes_dev), same buffers
     work_bytes = max(dqmc.dqmc_workspace_bytes(int(n)) for n in set(ns.tolist()))
@@ -576,11 +600,11 @@ def run_batched(args, rank, world, local, emit=True):
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / K
     return report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, same, False, tune_s, tune_ms,
-                          table, e2e_s, emit)
+                          table, e2e_s, emit, one)
 
 
 def report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, same, skipped, tune_s, tune_ms,
-                   table, e2e_s, emit=True):
+                   table, e2e_s, emit=True, one=None):
     K = args.steps
     cubes = int(sum(3 ** int(n) for n in ns))
     value = world * nf / (ms / 1e3)
@@ -602,6 +626,7 @@ def report_batched(args, rank, world, b, nf, ns, total, ms, clocks, ms_single, s
             "api": "dqmc_primes_dev, one call per function"},
         "speedup_vs_one_launch_per_function": None if skipped else ms_single / ms,
         "results_identical": same,
+        "one_persistent_launch": one,
         "launch_table": {"autotuned": not args.no_autotune, "seconds": tune_s,
                          "best_ms_per_n": tune_ms, "config_per_n": table},
         "e2e": None if e2e_s is None else {

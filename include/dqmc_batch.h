@@ -101,6 +101,22 @@ int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, con
                    const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps, const uint64_t *bm_off,
                    void *stream);
 
+/* dqmc_batch_run in one persistent launch (captured in the graph after the
+ * zeroing of the counts and of one queue counter per n): one CTA of 1024
+ * threads per SM takes the batch's n in turn, largest first, splitting its
+ * threads and shared memory into groups of that n's shape, and each group
+ * takes whole functions one at a time from the n's queue (n <= 4: one warp
+ * per function, cubes tested against the definitions; 5 <= n <= 13: the
+ * n's SMEM shape from the launch table when it is one CTA per function,
+ * else the built-in one, as many functions at once as the CTA's threads and
+ * shared memory hold; n = 14: the whole CTA, the thirds of the top digit in
+ * turn).  Same arguments, rules, workspace, results and errors as
+ * dqmc_batch_run; the two share the cached graph, so switching between them
+ * captures a new one. */
+int dqmc_batch_run_one_launch(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
+                              const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps,
+                              const uint64_t *bm_off, void *stream);
+
 /* Bytes of device workspace a batch with these n's takes (function tables,
  * control blocks and states of the n = 13, 14 functions on the TILES path,
  * the n = 14 scratch slots), sized for the configurations set now and the

@@ -111,6 +111,7 @@ struct BatchLayout {
     uint64_t state_off[kClasses] = {};
     uint64_t scratch_off = 0;       // n = 14 in one CTA: a third per CTA slot
     uint32_t scratch_ctas = 0;
+    uint64_t ctr_off = 0;           // one-launch mode: a queue counter per n
     uint64_t total = 0;
 };
 
@@ -152,6 +153,8 @@ BatchLayout batch_layout(uint32_t nfun, const uint32_t count[kClasses], const Cl
         L.scratch_off = at;
         at = align_up_b(at + (uint64_t)L.scratch_ctas * kFnThirdBytes, 256);
     }
+    L.ctr_off = at;
+    at = align_up_b(at + 4ull * kClasses, 256);
     L.total = at;
     return L;
 }
@@ -166,6 +169,7 @@ struct BatchCache {
     cudaEvent_t t0 = nullptr, t1 = nullptr;     // autotuner timing
     cudaGraphExec_t exec = nullptr;
     uint64_t cfg_gen = 0;
+    bool one = false;           // captured as one persistent launch
     // what the graph was captured for
     std::vector<uint32_t> n;
     std::vector<uint64_t> tt, dc, bm;
@@ -207,9 +211,11 @@ BatchCache *batch_cache(int *st)
 }
 
 bool same_batch(const BatchCache &c, uint32_t nfun, const uint32_t *n, const uint64_t *tt, const uint64_t *dc,
-                const uint64_t *bm, const void *arena, void *counts, void *bitmaps, uint64_t gen)
+                const uint64_t *bm, const void *arena, void *counts, void *bitmaps, uint64_t gen, bool one)
 {
-    if (!c.exec || c.cfg_gen != gen || c.n.size() != nfun || c.arena != arena || c.counts != counts || c.bitmaps != bitmaps) return false;
+    if (!c.exec || c.cfg_gen != gen || c.one != one || c.n.size() != nfun || c.arena != arena || c.counts != counts ||
+        c.bitmaps != bitmaps)
+        return false;
     if (c.has_dc != (dc != nullptr)) return false;
     if (memcmp(c.n.data(), n, 4ull * nfun) || memcmp(c.tt.data(), tt, 8ull * nfun) ||
         memcmp(c.bm.data(), bm, 8ull * nfun))
@@ -302,6 +308,49 @@ cudaError_t launch_class(BatchCache &c, const BatchLayout &L, int cl, const Clas
                         work + L.ctrl_off[cl], s, 0, plan_passes(p), &b);
 }
 
+// The one-launch shape of each n present, largest n first (launch_fn_queue):
+// the n's shared-memory shape from the launch table when it is one CTA per
+// function, else the built-in one; as many groups as the CTA's threads,
+// its shared memory and the named barriers allow.
+QueueSetup queue_setup(const BatchLayout &L, const uint32_t count[kClasses], const uint32_t class_at[kClasses],
+                       const ClassConfig cfg[kClasses], void *work)
+{
+    QueueSetup q;
+    for (int cl = kClasses - 1; cl >= 0; --cl) {
+        if (!count[cl]) continue;
+        QueueClass k;
+        k.n = (uint32_t)cl;
+        k.first = class_at[cl];
+        k.count = count[cl];
+        if (cl < kFnMinN) {
+            k.tg = 32;
+            k.groups = kQueueThreads / 32;
+        } else {
+            const ClassConfig cc = (cfg[cl].path == DQMC_BATCH_PATH_SMEM && cfg[cl].fn.ctas == 1) ? cfg[cl]
+                                                                                                     : default_config(cl);
+            k.digits = (uint32_t)cc.fn.digits;
+            if (cl == 14) {
+                k.tg = kQueueThreads;
+                k.groups = 1;
+            } else {
+                k.tg = (uint32_t)(cc.fn.tg == 64 ? 128 : cc.fn.tg);
+                uint32_t g = kQueueThreads / k.tg;
+                const uint64_t by_smem = kFnMaxSmem / queue_fn_smem(cl);
+                if (g > by_smem) g = (uint32_t)by_smem;
+                if (k.tg > 32 && g > 15) g = 15;
+                k.groups = g;
+            }
+        }
+        const uint64_t sm = (uint64_t)k.groups * queue_fn_smem(cl);
+        if (sm > q.smem) q.smem = sm;
+        q.cls[q.nclass++] = k;
+    }
+    q.ctr = reinterpret_cast<uint32_t *>(static_cast<char *>(work) + L.ctr_off);
+    q.ctas = thirds_slots();
+    if (count[14] && L.scratch_ctas < q.ctas) q.ctas = L.scratch_ctas;
+    return q;
+}
+
 }  // namespace
 
 cudaError_t launch_batch_in_smem(int n, const BatchArgs &b, cudaStream_t s)
@@ -333,9 +382,11 @@ extern "C" uint64_t dqmc_batch_workspace_bytes(uint32_t nfun, const uint32_t *n)
     return batch_layout(nfun, count, cfg).total;
 }
 
-extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
-                              const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps,
-                              const uint64_t *bm_off, void *stream)
+// dqmc_batch_run and dqmc_batch_run_one_launch: the graph is captured once
+// per batch (and mode) and launched again for the same batch.
+static int batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
+                     const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps, const uint64_t *bm_off,
+                     void *stream, bool one)
 {
     if (nfun == 0) return DQMC_OK;
     uint32_t count[kClasses];
@@ -348,11 +399,13 @@ extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *
     uint64_t gen = 0;
     config_snapshot(cfg, &gen);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (same_batch(*c, nfun, n, tt_off, dc_off, bm_off, d_tt_arena, d_out_count, d_out_bitmaps, gen))
+    if (same_batch(*c, nfun, n, tt_off, dc_off, bm_off, d_tt_arena, d_out_count, d_out_bitmaps, gen, one))
         return map_err(cudaGraphLaunch(c->exec, s));
 
     // ---- new batch: workspace, function tables, then capture the graph:
-    // zero the counts, then one branch per n (largest n first), joined at the end
+    // zero the counts, then one branch per n (largest n first), joined at the
+    // end; or, in one-launch mode, zero the queue counters and launch the
+    // queue kernel once
     const BatchLayout L = batch_layout(nfun, count, cfg);
     uint32_t class_at[kClasses];
     st = upload_tables(*c, L, nfun, n, tt_off, dc_off, bm_off, class_at, s);
@@ -363,24 +416,44 @@ extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return map_err(e);
     cudaError_t le = cudaMemsetAsync(d_out_count, 0, 8ull * nfun, cs);
-    if (le == cudaSuccess) le = cudaEventRecord(c->fork, cs);
-    bool joined[kClasses] = {};
-    for (int cl = kClasses - 1; cl >= 0 && le == cudaSuccess; --cl) {
-        if (!count[cl]) continue;
-        cudaStream_t bs = c->branch[cl];
-        le = cudaStreamWaitEvent(bs, c->fork, 0);
-        if (le == cudaSuccess)
-            le = launch_class(*c, L, cl, cfg[cl], class_at[cl], count[cl], d_tt_arena, d_out_count, d_out_bitmaps, bs);
-        if (le == cudaSuccess) le = cudaEventRecord(c->join[cl], bs);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, c->join[cl], 0);
-        joined[cl] = le == cudaSuccess;
-    }
-    // every branch that was forked must be joined before the capture ends
-    for (int cl = 0; cl < kClasses && le != cudaSuccess; ++cl)
-        if (count[cl] && !joined[cl]) {
-            cudaEventRecord(c->join[cl], c->branch[cl]);
-            cudaStreamWaitEvent(cs, c->join[cl], 0);
+    if (one) {
+        const QueueSetup q = queue_setup(L, count, class_at, cfg, c->work);
+        BatchArgs b;
+        char *work = static_cast<char *>(c->work);
+        b.fn = reinterpret_cast<const uint32_t *>(work + L.fn_off);
+        b.nfun = nfun;
+        b.tt_off = reinterpret_cast<const uint64_t *>(work + L.tt_off);
+        b.dc_off = reinterpret_cast<const uint64_t *>(work + L.dc_off);
+        b.bm_off = reinterpret_cast<const uint64_t *>(work + L.bm_off);
+        b.arena = static_cast<const uint8_t *>(d_tt_arena);
+        b.bitmaps = static_cast<uint8_t *>(d_out_bitmaps);
+        b.count = reinterpret_cast<unsigned long long *>(d_out_count);
+        if (L.scratch_ctas) {
+            b.scratch = work + L.scratch_off;
+            b.scratch_ctas = L.scratch_ctas;
         }
+        if (le == cudaSuccess) le = cudaMemsetAsync(q.ctr, 0, 4ull * kClasses, cs);
+        if (le == cudaSuccess) le = launch_fn_queue(b, q, cs);
+    } else {
+        if (le == cudaSuccess) le = cudaEventRecord(c->fork, cs);
+        bool joined[kClasses] = {};
+        for (int cl = kClasses - 1; cl >= 0 && le == cudaSuccess; --cl) {
+            if (!count[cl]) continue;
+            cudaStream_t bs = c->branch[cl];
+            le = cudaStreamWaitEvent(bs, c->fork, 0);
+            if (le == cudaSuccess)
+                le = launch_class(*c, L, cl, cfg[cl], class_at[cl], count[cl], d_tt_arena, d_out_count, d_out_bitmaps, bs);
+            if (le == cudaSuccess) le = cudaEventRecord(c->join[cl], bs);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, c->join[cl], 0);
+            joined[cl] = le == cudaSuccess;
+        }
+        // every branch that was forked must be joined before the capture ends
+        for (int cl = 0; cl < kClasses && le != cudaSuccess; ++cl)
+            if (count[cl] && !joined[cl]) {
+                cudaEventRecord(c->join[cl], c->branch[cl]);
+                cudaStreamWaitEvent(cs, c->join[cl], 0);
+            }
+    }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -403,7 +476,22 @@ extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *
     c->counts = d_out_count;
     c->bitmaps = d_out_bitmaps;
     c->cfg_gen = gen;
+    c->one = one;
     return map_err(cudaGraphLaunch(c->exec, s));
+}
+
+extern "C" int dqmc_batch_run(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off, const void *d_tt_arena,
+                              const uint64_t *dc_off, uint64_t *d_out_count, void *d_out_bitmaps,
+                              const uint64_t *bm_off, void *stream)
+{
+    return batch_run(nfun, n, tt_off, d_tt_arena, dc_off, d_out_count, d_out_bitmaps, bm_off, stream, false);
+}
+
+extern "C" int dqmc_batch_run_one_launch(uint32_t nfun, const uint32_t *n, const uint64_t *tt_off,
+                                         const void *d_tt_arena, const uint64_t *dc_off, uint64_t *d_out_count,
+                                         void *d_out_bitmaps, const uint64_t *bm_off, void *stream)
+{
+    return batch_run(nfun, n, tt_off, d_tt_arena, dc_off, d_out_count, d_out_bitmaps, bm_off, stream, true);
 }
 
 extern "C" int dqmc_batch_get_config(uint32_t n, dqmc_batch_config *out)

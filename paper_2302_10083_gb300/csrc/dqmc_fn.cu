@@ -334,20 +334,63 @@ __global__ void __launch_bounds__(1024, 1) fn_kernel(const FnArgs a)
     }
 }
 
-// n = 14 in one CTA: the three thirds of the top high digit one after the
-// other (persistent: CTA b takes functions b, b + grid, ...).  The '*' third
-// is merged first and parked in a scratch slot of the CTA's own in device
-// memory (210 KB, read back from L2); thirds 0 and 1 are merged, cleared by
-// it (Reduce of the top digit), reduced and written out; then the '*' third
-// comes back, is reduced and written out.
+// n = 14 by one thread group: the three thirds of the top high digit one after
+// the other.  The '*' third is merged first and parked in T (a scratch slot
+// of the group's own in device memory, 210 KB, read back from L2); thirds 0
+// and 1 are merged, cleared by it (Reduce of the top digit), reduced and
+// written out; then the '*' third comes back, is reduced and written out.
+template <int D, typename Sync>
+__device__ __forceinline__ void fn_thirds_one(const uint32_t *on, const uint32_t *dc, uint32_t *out,
+                                              unsigned long long *count, uint64_t out_words, uint64_t alloc_words,
+                                              uint4 *S, uint4 *T, int lt, int tg, const Sync &sync)
+{
+    constexpr int HL = 8, R = (int)pow3(HL);
+    unsigned long long bits = 0;
+    load_rows<HL, 1>(S, on, dc, 2, lt, tg);
+    sync();
+    merge_all<HL, 0, D>(S, lt, tg, sync);
+    for (int i = lt; i < 2 * R; i += tg) T[i] = S[i];
+    sync();   // the scratch copy is complete (and visible to the group) before S is reused
+    for (int part = 0; part < 2; ++part) {
+        load_rows<HL, 1>(S, on, dc, part, lt, tg);
+        sync();
+        merge_all<HL, 0, D>(S, lt, tg, sync);
+        for (int i = lt; i < 2 * R; i += tg) {
+            const uint4 z = T[i];
+            uint4 v = S[i];
+            v.x &= ~z.x; v.y &= ~z.y; v.z &= ~z.z; v.w &= ~z.w;
+            S[i] = v;
+        }
+        sync();
+        reduce_all<HL, 0, D>(S, lt, tg, sync);
+        if (part == 0) {
+            bits += chunk_pack<R, true>(S, out, lt, tg);   // third 0 starts at bit 0
+        } else {
+            bits += chunk_pack<R, false>(S, out, lt, tg);
+            sync();
+            stream_out<R>(S, out, part, 3, out_words, alloc_words, lt, tg);
+        }
+        sync();
+    }
+    for (int i = lt; i < 2 * R; i += tg) S[i] = T[i];
+    sync();
+    reduce_all<HL, 0, D>(S, lt, tg, sync);
+    bits += chunk_pack<R, false>(S, out, lt, tg);
+    sync();
+    stream_out<R>(S, out, 2, 3, out_words, alloc_words, lt, tg);
+    add_count(count, bits);
+    sync();   // S and T are free for the next function
+}
+
+// n = 14 in one CTA (persistent: CTA b takes functions b, b + grid, ...),
+// with the CTA's scratch slot.
 template <int D>
 __global__ void __launch_bounds__(1024, 1) fn_thirds_kernel(const FnArgs a)
 {
-    constexpr int HL = 8, R = (int)pow3(HL);
+    constexpr int R = (int)pow3(8);
     extern __shared__ uint4 fsmem[];
     const int tg = (int)blockDim.x, lt = (int)threadIdx.x;
     const SubSync sync{1, tg, true};
-    uint4 *S = fsmem;
     uint4 *T = a.scratch + (size_t)blockIdx.x * 2 * R;
     for (uint64_t fi = blockIdx.x; fi < a.nfun; fi += gridDim.x) {
         const uint32_t id = a.fn[fi];
@@ -355,42 +398,7 @@ __global__ void __launch_bounds__(1024, 1) fn_thirds_kernel(const FnArgs a)
         const uint64_t dco = a.dc_off[id];
         const uint32_t *dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(a.arena + dco);
         uint32_t *out = reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]);
-        unsigned long long bits = 0;
-
-        load_rows<HL, 1>(S, on, dc, 2, lt, tg);
-        sync();
-        merge_all<HL, 0, D>(S, lt, tg, sync);
-        for (int i = lt; i < 2 * R; i += tg) T[i] = S[i];
-        sync();   // the scratch copy is complete (and visible to the block) before S is reused
-        for (int part = 0; part < 2; ++part) {
-            load_rows<HL, 1>(S, on, dc, part, lt, tg);
-            sync();
-            merge_all<HL, 0, D>(S, lt, tg, sync);
-            for (int i = lt; i < 2 * R; i += tg) {
-                const uint4 z = T[i];
-                uint4 v = S[i];
-                v.x &= ~z.x; v.y &= ~z.y; v.z &= ~z.z; v.w &= ~z.w;
-                S[i] = v;
-            }
-            sync();
-            reduce_all<HL, 0, D>(S, lt, tg, sync);
-            if (part == 0) {
-                bits += chunk_pack<R, true>(S, out, lt, tg);   // third 0 starts at bit 0
-            } else {
-                bits += chunk_pack<R, false>(S, out, lt, tg);
-                sync();
-                stream_out<R>(S, out, part, 3, a.out_words, a.out_alloc_words, lt, tg);
-            }
-            sync();
-        }
-        for (int i = lt; i < 2 * R; i += tg) S[i] = T[i];
-        sync();
-        reduce_all<HL, 0, D>(S, lt, tg, sync);
-        bits += chunk_pack<R, false>(S, out, lt, tg);
-        sync();
-        stream_out<R>(S, out, 2, 3, a.out_words, a.out_alloc_words, lt, tg);
-        add_count(a.count + id, bits);
-        sync();   // S and T are free for the next function
+        fn_thirds_one<D>(on, dc, out, a.count + id, a.out_words, a.out_alloc_words, fsmem, T, lt, tg, sync);
     }
 }
 
@@ -473,6 +481,211 @@ bool fn_config_ok(int n, const FnConfig &c)
     if (c.ctas != 1 && c.ctas != 3 && c.ctas != 9) return false;
     if (c.ctas > 1 && c.fpc != 1) return false;
     return fn_smem_bytes(n, c.fpc, c.ctas) <= kFnMaxSmem;
+}
+
+// ------------------------------------------------- the batch in one launch
+// (launch_fn_queue, dqmc_internal.h.)  Thread groups synchronise with a
+// named barrier of their own (barrier 1 + group), or __syncwarp for a group
+// of one warp.
+struct GroupSync {
+    int id, nthreads;
+    __device__ __forceinline__ void operator()() const
+    {
+        if (nthreads == 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+    }
+};
+
+struct QueueArgs {
+    const uint32_t *fn;
+    const uint64_t *tt_off, *dc_off, *bm_off;
+    const uint8_t *arena;
+    uint8_t *bitmaps;
+    unsigned long long *count;
+    uint32_t *ctr;
+    uint4 *scratch;                 // n = 14: 3^8 rows per CTA of the grid
+    uint32_t nclass;
+    QueueClass cls[kFnMaxN + 1];
+};
+
+// shared memory of one function of n in the queue kernel: its rows (one third
+// of them at n = 14), none below n = 5
+__host__ __device__ constexpr uint64_t queue_fn_smem_d(int n)
+{
+    return n < kFnMinN ? 0 : pow3((n == 14 ? 13 : n) - kChunkDigits) * kChunkBytes;
+}
+
+// bitmap slot of an n-variable function in 32-bit words: ceil(3^n / 8) bytes
+// rounded up to 16
+__host__ __device__ constexpr uint64_t slot_words(int n) { return ((pow3(n) + 7) / 8 + 15) / 16 * 4; }
+
+// n <= 4 by one warp, from the definitions (at most 81 cubes): a cube is an
+// implicant when every minterm it covers is in ON or DC, a prime when it is
+// an implicant and none of its one-digit extensions (a 0/1 digit made '*')
+// is.  Cube q = lane + 32 k; its bit in the bitmap is bit q.
+__device__ __forceinline__ void tiny_one(int n, const uint8_t *on, const uint8_t *dc, uint32_t *out,
+                                         unsigned long long *count)
+{
+    const int lane = (int)threadIdx.x & 31;
+    const int N3 = (int)pow3(n);
+    uint32_t imp[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = lane + 32 * k;
+        bool is = false;
+        if (q < N3) {
+            int base = 0, stars = 0, x = q;
+            for (int i = 0; i < n; ++i, x /= 3) {
+                const int d = x % 3;
+                if (d == 2) stars |= 1 << i;
+                else base |= d << i;
+            }
+            is = true;
+            for (int sub = stars;; sub = (sub - 1) & stars) {   // every subset of the '*' digits
+                const int m = base | sub;
+                const uint32_t cell = on[m >> 3] | (dc ? dc[m >> 3] : 0u);
+                if (!((cell >> (m & 7)) & 1u)) is = false;
+                if (sub == 0) break;
+            }
+        }
+        imp[k] = __ballot_sync(0xffffffffu, is);
+    }
+    auto implicant = [&](int q) -> bool { return (imp[q >> 5] >> (q & 31)) & 1u; };
+    uint32_t pw[3];
+    unsigned long long bits = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = lane + 32 * k;
+        bool pr = false;
+        if (q < N3 && implicant(q)) {
+            pr = true;
+            int x = q, w = 1;
+            for (int i = 0; i < n; ++i, x /= 3, w *= 3) {
+                const int d = x % 3;
+                if (d != 2 && implicant(q + (2 - d) * w)) pr = false;
+            }
+        }
+        pw[k] = __ballot_sync(0xffffffffu, pr);
+        bits += __popc(pw[k]);
+    }
+    static_assert(slot_words(4) == 4, "n <= 4: a 16-byte bitmap slot");
+    if (lane < 4) out[lane] = lane < 3 ? pw[lane] : 0u;
+    if (lane == 0 && bits) atomicAdd(count, bits);
+}
+
+// 5 <= n <= 13 by one thread group, the whole function in S.
+template <int HL, int D, typename Sync>
+__device__ __forceinline__ void whole_one(const QueueArgs &a, uint32_t id, uint4 *S, int lt, int tg, const Sync &sync)
+{
+    constexpr int R = (int)pow3(HL);
+    const uint32_t *on = reinterpret_cast<const uint32_t *>(a.arena + a.tt_off[id]);
+    const uint64_t dco = a.dc_off[id];
+    const uint32_t *dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(a.arena + dco);
+    uint32_t *out = reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]);
+    load_rows<HL, 0>(S, on, dc, 0, lt, tg);
+    sync();
+    merge_all<HL, 0, D>(S, lt, tg, sync);
+    reduce_all<HL, 0, D>(S, lt, tg, sync);
+    add_count(a.count + id, chunk_pack<R, true>(S, out, lt, tg));
+    constexpr uint64_t NP = ((uint64_t)R * pow3(kChunkDigits) + 31) / 32;
+    for (uint64_t w = NP + lt; w < slot_words(HL + kChunkDigits); w += tg) out[w] = 0u;   // at most three words
+}
+
+template <int D, typename Sync>
+__device__ __forceinline__ void queue_one(const QueueArgs &a, int n, uint32_t id, uint4 *S, int lt, int tg,
+                                          const Sync &sync)
+{
+    switch (n) {
+    case 5: whole_one<0, D>(a, id, S, lt, tg, sync); break;
+    case 6: whole_one<1, D>(a, id, S, lt, tg, sync); break;
+    case 7: whole_one<2, D>(a, id, S, lt, tg, sync); break;
+    case 8: whole_one<3, D>(a, id, S, lt, tg, sync); break;
+    case 9: whole_one<4, D>(a, id, S, lt, tg, sync); break;
+    case 10: whole_one<5, D>(a, id, S, lt, tg, sync); break;
+    case 11: whole_one<6, D>(a, id, S, lt, tg, sync); break;
+    case 12: whole_one<7, D>(a, id, S, lt, tg, sync); break;
+    case 13: whole_one<8, D>(a, id, S, lt, tg, sync); break;
+    case 14: {
+        const uint32_t *on = reinterpret_cast<const uint32_t *>(a.arena + a.tt_off[id]);
+        const uint64_t dco = a.dc_off[id];
+        const uint32_t *dc = dco == ~0ull ? nullptr : reinterpret_cast<const uint32_t *>(a.arena + dco);
+        uint32_t *out = reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]);
+        uint4 *T = a.scratch + (size_t)blockIdx.x * 2 * pow3(8);
+        fn_thirds_one<D>(on, dc, out, a.count + id, (pow3(14) + 31) / 32, slot_words(14), S, T, lt, tg, sync);
+        break;
+    }
+    default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kQueueThreads, 1) fn_queue_kernel(const __grid_constant__ QueueArgs a)
+{
+    extern __shared__ uint4 qsmem[];
+    __shared__ uint32_t item[32];
+    const int tid = (int)threadIdx.x;
+    for (uint32_t c = 0; c < a.nclass; ++c) {
+        const QueueClass k = a.cls[c];
+        const int tg = (int)k.tg, sub = tid / tg, lt = tid - sub * tg;
+        if (sub < (int)k.groups) {
+            const GroupSync sync{1 + sub, tg};
+            uint4 *S = qsmem + (size_t)sub * (queue_fn_smem_d((int)k.n) / 16);
+            for (;;) {
+                if (lt == 0) item[sub] = atomicAdd(a.ctr + c, 1u);
+                sync();
+                const uint32_t i = item[sub];
+                if (i >= k.count) break;
+                const uint32_t id = a.fn[k.first + i];
+                if (k.n <= 4) {
+                    const uint64_t dco = a.dc_off[id];
+                    tiny_one((int)k.n, a.arena + a.tt_off[id], dco == ~0ull ? nullptr : a.arena + dco,
+                             reinterpret_cast<uint32_t *>(a.bitmaps + a.bm_off[id]), a.count + id);
+                } else if (k.digits >= 3) {
+                    queue_one<3>(a, (int)k.n, id, S, lt, tg, sync);
+                } else {
+                    queue_one<2>(a, (int)k.n, id, S, lt, tg, sync);
+                }
+                sync();   // every thread has read item[sub] and is done with S
+            }
+        }
+        __syncthreads();   // the next n splits the CTA (and its shared memory) its own way
+    }
+}
+
+uint64_t queue_fn_smem(int n) { return queue_fn_smem_d(n); }
+
+cudaError_t launch_fn_queue(const BatchArgs &b, const QueueSetup &q, cudaStream_t s)
+{
+    if (q.nclass == 0 || q.nclass > kFnMaxN + 1 || !q.ctr || q.ctas == 0 || q.smem > kFnMaxSmem)
+        return cudaErrorInvalidValue;
+    QueueArgs a{};
+    a.fn = b.fn;
+    a.tt_off = b.tt_off;
+    a.dc_off = b.dc_off;
+    a.bm_off = b.bm_off;
+    a.arena = b.arena;
+    a.bitmaps = b.bitmaps;
+    a.count = b.count;
+    a.ctr = q.ctr;
+    a.scratch = static_cast<uint4 *>(b.scratch);
+    a.nclass = q.nclass;
+    for (uint32_t c = 0; c < q.nclass; ++c) {
+        const QueueClass &k = q.cls[c];
+        // the shapes the kernel takes: a warp per function below n = 5, the
+        // whole CTA (with a scratch slot) at n = 14, named barriers 1 .. 15
+        if (k.n > (uint32_t)kFnMaxN || k.tg < 32 || k.tg % 32 || k.groups == 0 || k.tg * k.groups > kQueueThreads)
+            return cudaErrorInvalidValue;
+        if ((k.n < (uint32_t)kFnMinN && k.tg != 32) || (k.n == 14 && (k.tg != kQueueThreads || !b.scratch ||
+                                                                       b.scratch_ctas < q.ctas)))
+            return cudaErrorInvalidValue;
+        if (k.tg > 32 && k.groups > 15) return cudaErrorInvalidValue;
+        if (k.digits != 2 && k.digits != 3) return cudaErrorInvalidValue;
+        if (k.groups * queue_fn_smem((int)k.n) > q.smem) return cudaErrorInvalidValue;
+        a.cls[c] = k;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+    if (e != cudaSuccess) return e;
+    fn_queue_kernel<<<q.ctas, kQueueThreads, q.smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fn_batch(int n, const BatchArgs &b, const FnConfig &c, cudaStream_t s)

@@ -202,6 +202,30 @@ bool fn_config_ok(int n, const FnConfig &c);
 // Counts are not zeroed; bitmaps and counts come from the batch tables.
 cudaError_t launch_fn_batch(int n, const BatchArgs &b, const FnConfig &c, cudaStream_t s);
 
+// The batch in one persistent launch (dqmc_fn.cu): one CTA of kQueueThreads
+// threads per SM; the functions of each n wait in a queue of their own (ids
+// b.fn[first .. first + count)), the queues largest n first.  A CTA takes the
+// queues in turn, split into `groups` thread groups of tg threads for that n;
+// a group takes one function at a time from the queue's counter (ctr[class],
+// zeroed before the launch).  n <= 4: one warp per function; 5 <= n <= 13:
+// the whole function in shared memory, `digits` high digits per step;
+// n = 14: the whole CTA, the thirds of the top digit in turn with the CTA's
+// scratch slot (b.scratch, at least `ctas` slots).
+constexpr int kQueueThreads = 1024;
+struct QueueClass {
+    uint32_t n = 0, first = 0, count = 0;
+    uint32_t tg = 32, groups = 1, digits = 3;
+};
+struct QueueSetup {
+    uint32_t nclass = 0;
+    QueueClass cls[kFnMaxN + 1];
+    uint32_t *ctr = nullptr;
+    uint32_t ctas = 0;
+    uint64_t smem = 0;          // dynamic shared memory of the launch
+};
+uint64_t queue_fn_smem(int n);  // shared memory one function of n takes in the queue kernel
+cudaError_t launch_fn_queue(const BatchArgs &b, const QueueSetup &q, cudaStream_t s);
+
 // Sweep a batch of functions of one n <= 14 without device state: the
 // shared-memory kernel with the batch table's shape for n (the built-in
 // shared-memory shape if the table says the tile path), the one-tile kernel

@@ -147,25 +147,25 @@ __device__ __forceinline__ void reduce_step(uint4 *S, int lt, int tg)
     }
 }
 
-template <int HL, int J, int D>
-__device__ __forceinline__ void merge_all(uint4 *S, int lt, int tg, const SubSync &sync)
+template <int HL, int J, int D, typename Sync>
+__device__ __forceinline__ void merge_all(uint4 *S, int lt, int tg, const Sync &sync)
 {
     if constexpr (J < HL) {
         constexpr int DD = (HL - J < D) ? HL - J : D;
         merge_step<HL, J, DD>(S, lt, tg);
         sync();
-        merge_all<HL, J + DD, D>(S, lt, tg, sync);
+        merge_all<HL, J + DD, D, Sync>(S, lt, tg, sync);
     }
 }
 
-template <int HL, int J, int D>
-__device__ __forceinline__ void reduce_all(uint4 *S, int lt, int tg, const SubSync &sync)
+template <int HL, int J, int D, typename Sync>
+__device__ __forceinline__ void reduce_all(uint4 *S, int lt, int tg, const Sync &sync)
 {
     if constexpr (J < HL) {
         constexpr int DD = (HL - J < D) ? HL - J : D;
         reduce_step<HL, J, DD>(S, lt, tg);
         sync();
-        reduce_all<HL, J + DD, D>(S, lt, tg, sync);
+        reduce_all<HL, J + DD, D, Sync>(S, lt, tg, sync);
     }
 }
 

@@ -79,6 +79,8 @@ _SIGS = {
     "dqmc_primes_dev_static": (ctypes.c_int, [ctypes.c_uint32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dqmc_dev_status_static": (ctypes.c_int, [ctypes.c_uint32, c_vp]),
     "dqmc_batch_run": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p, c_vp]),
+    "dqmc_batch_run_one_launch": (ctypes.c_int, [ctypes.c_uint32, c_u32p, c_u64p, c_vp, c_u64p, c_vp, c_vp, c_u64p,
+                                                 c_vp]),
     "dqmc_batch_workspace_bytes": (ctypes.c_uint64, [ctypes.c_uint32, c_u32p]),
     "dqmc_batch_release": (ctypes.c_int, []),
     "dqmc_batch_get_config": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32 * 5)]),
@@ -419,10 +421,11 @@ def dqmc_batch_workspace_bytes(ns) -> int:
     return int(lib().dqmc_batch_workspace_bytes(len(a), p))
 
 
-def dqmc_batch_run(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, stream) -> int:
-    """dqmc_batch_run: ns / tt_off / dc_off / bm_off are host arrays (dc_off may
-    be None), the d_* arguments device pointers (ints), stream a cudaStream_t
-    (int or None).  Returns the status."""
+def dqmc_batch_run(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, stream, one_launch=False) -> int:
+    """dqmc_batch_run (one_launch: dqmc_batch_run_one_launch): ns / tt_off /
+    dc_off / bm_off are host arrays (dc_off may be None), the d_* arguments
+    device pointers (ints), stream a cudaStream_t (int or None).  Returns the
+    status."""
     n_a, n_p = _host_u32(ns)
     tt_a, tt_p = _host_u64(tt_off)
     bm_a, bm_p = _host_u64(bm_off)
@@ -430,7 +433,8 @@ def dqmc_batch_run(ns, tt_off, d_arena, dc_off, d_counts, d_bitmaps, bm_off, str
         dc_a, dc_p = None, None
     else:
         dc_a, dc_p = _host_u64(dc_off)
-    return lib().dqmc_batch_run(len(n_a), n_p, tt_p, d_arena, dc_p, d_counts, d_bitmaps, bm_p, stream)
+    fn = lib().dqmc_batch_run_one_launch if one_launch else lib().dqmc_batch_run
+    return fn(len(n_a), n_p, tt_p, d_arena, dc_p, d_counts, d_bitmaps, bm_p, stream)
 
 
 def dqmc_batch_release() -> int:

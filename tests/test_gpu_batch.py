@@ -43,7 +43,7 @@ def set_all(path, **shape):
             assert dqmc.dqmc_batch_set_config(n, cfg) == dqmc.DQMC_OK
 
 
-def run_batch(b, with_dc=True):
+def run_batch(b, with_dc=True, one_launch=False):
     ns = b["n"].astype(np.uint32)
     dev = "cuda:0"
     arena = torch.from_numpy(b["arena"]).to(dev)
@@ -53,7 +53,7 @@ def run_batch(b, with_dc=True):
     stream = torch.cuda.current_stream().cuda_stream
     dc_off = b["dc_off"] if with_dc else None
     st = dqmc.dqmc_batch_run(ns, b["tt_off"], arena.data_ptr(), dc_off, counts.data_ptr(), bitmaps.data_ptr(),
-                             bm_off, stream)
+                             bm_off, stream, one_launch=one_launch)
     assert st == dqmc.DQMC_OK, dqmc.strerror(st)
     torch.cuda.synchronize()
     return arena, bitmaps, counts, bm_off, dc_off
@@ -223,3 +223,87 @@ def test_autotune_then_run_bit_exact(table):
         assert dqmc.dqmc_batch_set_config(n, c) == dqmc.DQMC_OK
     _, bitmaps, counts, bm_off, dc_off = run_batch(b)
     check_batch(b, bitmaps, counts, bm_off, dc_off)
+
+
+# ------------------------------------------------------- one persistent launch
+
+def test_one_launch_mixed_sizes_bit_exact():
+    """dqmc_batch_run_one_launch on the workload's n = 4..14 mix with
+    don't-cares: every function bit-exact against the oracle; the graph
+    launched again gives the same; then the graph path on the same buffers
+    (a new capture) gives the same bytes."""
+    b = synth.batch_functions(count=240, seed=11)
+    arena, bitmaps, counts, bm_off, dc_off = run_batch(b, one_launch=True)
+    check_batch(b, bitmaps, counts, bm_off, dc_off)
+    first = bitmaps.clone()
+    bitmaps.fill_(0x5A)
+    counts.fill_(-1)
+    stream = torch.cuda.current_stream().cuda_stream
+    ns = b["n"].astype(np.uint32)
+    for one in (True, False):
+        st = dqmc.dqmc_batch_run(ns, b["tt_off"], arena.data_ptr(), dc_off, counts.data_ptr(), bitmaps.data_ptr(),
+                                 bm_off, stream, one_launch=one)
+        assert st == dqmc.DQMC_OK
+        torch.cuda.synchronize()
+        assert torch.equal(bitmaps, first)
+
+
+def test_one_launch_degenerate_and_small_n():
+    """n = 0..8 without a don't-care table (n <= 4 by one warp each, from the
+    definitions), and closed forms through the same launch: constant 1 (only
+    the all-'*' cube), constant 0 (no primes) and parity (its 2^(n-1)
+    minterms) for n = 0..14."""
+    b = synth.batch_functions(count=90, seed=12, n_lo=0, n_hi=8)
+    arena, bitmaps, counts, bm_off, dc_off = run_batch(b, with_dc=False, one_launch=True)
+    check_batch(b, bitmaps, counts, bm_off, None)
+    ns, tabs = [], []
+    for n in range(0, 15):
+        nb = ((1 << n) + 7) >> 3
+        x = np.arange(1 << n)
+        par = np.zeros(1 << n, dtype=np.uint8)
+        for i in range(n):
+            par ^= ((x >> i) & 1).astype(np.uint8)
+        for t in (np.full(nb, 0xFF, np.uint8) if n >= 3 else synth.pack(np.ones(1 << n, bool)),
+                  np.zeros(nb, np.uint8), synth.pack(par.astype(bool))):
+            ns.append(n)
+            tabs.append(np.asarray(t, np.uint8))
+    off, pos = [], 0
+    for t in tabs:
+        off.append(pos)
+        pos += (len(t) + 3) // 4 * 4
+    arena = np.zeros(pos, np.uint8)
+    for o, t in zip(off, tabs):
+        arena[o: o + len(t)] = t
+    bb = {"n": np.array(ns), "tt_off": np.array(off, np.uint64), "arena": arena,
+          "dc_off": np.full(len(ns), np.iinfo(np.uint64).max, np.uint64)}
+    _, bitmaps, counts, bm_off, _ = run_batch(bb, with_dc=False, one_launch=True)
+    cnt = counts.cpu().numpy()
+    bm = bitmaps.cpu().numpy()
+    for f, n in enumerate(ns):
+        kind = f % 3
+        want = [1, 0, 1 << (n - 1) if n else 0][kind]
+        assert int(cnt[f]) == want, (n, kind)
+        bits = np.unpackbits(bm[int(bm_off[f]): int(bm_off[f]) + (3 ** n + 7) // 8], bitorder="little")[: 3 ** n]
+        if kind == 0:
+            assert bits.sum() == 1 and bits[3 ** n - 1] == 1
+        elif kind == 1:
+            assert not bits.any()
+    check_batch(bb, bitmaps, counts, bm_off, None)
+
+
+def test_one_launch_large_classes_and_tuned_shapes(table):
+    """Only n = 12..14 (groups of 256 threads, the whole CTA, the thirds of
+    n = 14), then with every n's shared-memory shape set to 128 threads and
+    two digits per step: bit-exact both times."""
+    b = synth.batch_functions(count=30, seed=13, n_lo=12, n_hi=14)
+    arena, bitmaps, counts, bm_off, dc_off = run_batch(b, one_launch=True)
+    check_batch(b, bitmaps, counts, bm_off, dc_off)
+    for n in range(5, 15):
+        cfg = dict(path=dqmc.DQMC_BATCH_PATH_SMEM, threads_per_fn=128, fns_per_cta=1, digits_per_step=2,
+                   ctas_per_fn=1)
+        if n == 14:
+            cfg["threads_per_fn"] = 1024
+        assert dqmc.dqmc_batch_set_config(n, cfg) == dqmc.DQMC_OK
+    b2 = synth.batch_functions(count=120, seed=14, n_lo=5, n_hi=14)
+    arena, bitmaps, counts, bm_off, dc_off = run_batch(b2, one_launch=True)
+    check_batch(b2, bitmaps, counts, bm_off, dc_off)
