@@ -311,7 +311,8 @@ cudaError_t launch_class(BatchCache &c, const BatchLayout &L, int cl, const Clas
 // The one-launch shape of each n present, largest n first (launch_fn_queue):
 // the n's shared-memory shape from the launch table when it is one CTA per
 // function, else the built-in one; as many groups as the CTA's threads,
-// its shared memory and the named barriers allow.
+// its shared memory and the named barriers allow, and groups of more than
+// one warp widened to use all the threads (n = 12: 3 groups of 320).
 QueueSetup queue_setup(const BatchLayout &L, const uint32_t count[kClasses], const uint32_t class_at[kClasses],
                        const ClassConfig cfg[kClasses], void *work)
 {
@@ -339,6 +340,8 @@ QueueSetup queue_setup(const BatchLayout &L, const uint32_t count[kClasses], con
                 if (g > by_smem) g = (uint32_t)by_smem;
                 if (k.tg > 32 && g > 15) g = 15;
                 k.groups = g;
+                // when shared memory caps the groups, spread the CTA's threads over them
+                if (k.tg > 32 && g * k.tg < (uint32_t)kQueueThreads) k.tg = kQueueThreads / g / 32 * 32;
             }
         }
         const uint64_t sm = (uint64_t)k.groups * queue_fn_smem(cl);
