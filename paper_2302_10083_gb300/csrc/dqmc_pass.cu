@@ -269,6 +269,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
+// L2 prefetch of `bytes` (a multiple of 16) at a 16-byte aligned address.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Bitmap pass: the tile this many tickets later is brought into L2 when a
+// tile starts, so that its own bulk copies find it there (0: none).  About
+// two tiles per SM ahead (measured at n = 24: 0 / 76 / 152 / 228 / 304 / 456
+// / 912 tickets: 30.0 / 29.7 / 29.5 / 29.4 / 29.35 / 29.6 / 30.9 ms; further
+// ahead the lines leave L2 before they are used).
+constexpr uint64_t kPrefetchAhead = 304;
+
 // The first pass's tile layout: row r, half h.
 __device__ __forceinline__ int slotp(int r, int h) { return 2 * r + (h ^ ((r >> 2) & 1)); }
 
@@ -633,6 +646,11 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                     const char *src = reinterpret_cast<const char *>(&F.state[2 * S.base]);
                     for (int q = 0; q < 6; ++q)
                         bulk_g2s(reinterpret_cast<char *>(tile) + q * kPart, src + q * kPart, kPart, &S.bar);
+                    // the bitmap pass's tiles are contiguous in rho order: tile t
+                    // starts at row t 3^7
+                    const uint64_t t2 = S.tile + kPrefetchAhead;
+                    if (kPrefetchAhead && !P.bfn && t2 < P.out_tiles && (t2 + 1) * kTileRows <= P.state_rows)
+                        bulk_prefetch_l2(&F.state[2 * t2 * kTileRows], (uint32_t)(kTileRows * kChunkBytes));
                 } else {
                     S.load_fail = 2;   // a tile past the state (reported): not loaded, not swept
                 }
