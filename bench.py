@@ -319,6 +319,9 @@ def run_ours(args, rank, world, local):
     barrier()
     t_wall1 = time.time()
     buf.status()  # raises DqmcError if a bounded device wait gave up
+    count = int(buf.count.item())   # (also when no warm-up step ran)
+    if count > cap:
+        raise SystemExit(f"list overflow: {count} primes > cap {cap}")
     total_ms = start.elapsed_time(evs[K - 1][npass - 1])
     per_pass = [0.0] * npass
     for k in range(K):
@@ -398,8 +401,9 @@ def run_ours(args, rank, world, local):
 
 def batched_summary(args, local):
     """The batched workload (65,536 functions) as a compact object of the main
-    line: one graph launch per step against one dqmc_primes_dev call per
-    function, built-in launch table (the autotuner's choice on a GB300)."""
+    line: one graph launch per step (per-n kernels, and the same batch in one
+    persistent launch) against one dqmc_primes_dev call per function, built-in
+    launch table (the autotuner's choice on a GB300)."""
     a = argparse.Namespace(**vars(args))
     a.batch, a.batch_n, a.no_autotune, a.no_one_by_one, a.no_e2e = 65536, None, True, False, True
     a.steps, a.warmup = 10, 3
@@ -408,6 +412,7 @@ def batched_summary(args, local):
             "steps": a.steps, "one_launch_per_function": r["one_launch_per_function"],
             "speedup_vs_one_launch_per_function": r["speedup_vs_one_launch_per_function"],
             "results_identical": r["results_identical"], "cubes_per_s": r["cubes_per_s"],
+            "one_persistent_launch": r["one_persistent_launch"],
             "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "config": r["config"]}
 
 
