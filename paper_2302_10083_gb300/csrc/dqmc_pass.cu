@@ -788,8 +788,12 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
             // three digits per step with one barrier each (dqmc_steps.cuh); then
             // each thread reduces the chunk digits of its rows (if this pass has
             // any) and counts them.
-            const SubSync sync{1, NT, true};
-            reduce_all<kTileDigits, 0, kOutStepDigits>(tile, tid, NT, sync);
+            // Tile digits 0..5 in two steps; digit 6 in the row loop below.
+            static_assert(kTileDigits == 7 && kOutStepDigits == 3, "two steps of three digits, then digit 6");
+            reduce_step<kTileDigits, 0, 3>(tile, tid, NT);
+            __syncthreads();
+            reduce_step<kTileDigits, 3, 3>(tile, tid, NT);
+            __syncthreads();
             // Neighbour group (bitmap pass): a cell is also cleared when its
             // '*' neighbour in a neighbour-group digit is set in the state as
             // the previous pass left it.  The neighbour tiles are never
@@ -802,13 +806,22 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
             // A row with no set cell stays empty whatever its neighbours
             // hold, so it reads no neighbour row and skips the chunk digits
             // (the tile itself is always read and its bitmap always written).
+            // Tile digit 6 is reduced here too: a row whose digit 6 is 0/1
+            // reads its '*' row (729 or 1458 rows on) from the tile while the
+            // thread that owns that row may be writing it back reduced, so a
+            // bit is seen either as the two Reduce steps left it or final.
+            // Either is exact: a cell whose only implicant extensions are in
+            // digit 6 has its digit-6 extension prime, set in both; any other
+            // extension is cleared through the neighbour group (read from the
+            // state, unchanged in this pass) or the chunk digits (read from
+            // the row as the steps left it, before this thread changes it).
             const int n_nbr = (MODE == kModeOut) ? S.n_nbr : 0;
             const uint4 *const tile_g = state + 2 * base;
             for (int r = tid; r < kTileRows; r += NT) {
                 const uint4 q0 = tile[2 * r], q1 = tile[2 * r + 1];
                 uint32_t v[kChunkWords] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
                 const bool any = ((q0.x | q0.y | q0.z | q0.w) | (q1.x | q1.y | q1.z | q1.w)) != 0u;
-                if (any && (CM != 0 || n_nbr)) {
+                if (any) {
                     uint32_t acc[kChunkWords] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
                     for (int k = 0; k < kMaxNbr; ++k) {
@@ -819,11 +832,18 @@ __global__ void __launch_bounds__(unit_threads<MODE>(), 3) unit_pass_kernel(cons
                             acc[4] |= a1.x; acc[5] |= a1.y; acc[6] |= a1.z; acc[7] |= a1.w;
                         }
                     }
+                    constexpr int R6 = (int)pow3(kTileDigits - 1);   // 729 rows per value of digit 6
+                    if (r < 2 * R6) {
+                        const int rs = r + (r < R6 ? 2 * R6 : R6);   // the row with digit 6 = '*'
+                        const uint4 b0 = tile[2 * rs], b1 = tile[2 * rs + 1];
+                        acc[0] |= b0.x; acc[1] |= b0.y; acc[2] |= b0.z; acc[3] |= b0.w;
+                        acc[4] |= b1.x; acc[5] |= b1.y; acc[6] |= b1.z; acc[7] |= b1.w;
+                    }
                     if constexpr (CM != 0) chunk_reduce_p<CM>(v, acc);
 #pragma unroll
                     for (int w = 0; w < kChunkWords; ++w) v[w] &= ~acc[w];
-                    tile[2 * r] = make_uint4(v[0], v[1], v[2], v[3]);     // only this thread touches row r here
-                    tile[2 * r + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+                    tile[2 * r] = make_uint4(v[0], v[1], v[2], v[3]);     // only this thread writes row r here
+                    tile[2 * r + 1] = make_uint4(v[4], v[5], v[6], v[7]);   // (others may read it: digit 6)
                 }
 #pragma unroll
                 for (int w = 0; w < kChunkWords; ++w) my_count += __popc(v[w]);

@@ -195,3 +195,98 @@ def test_reversed_in_block_order_is_wrong():
     assert want.sum() == 1 and want[3 ** n - 1]   # f = 1: only the all-'*' cube
     assert np.array_equal(good, want)
     assert not np.array_equal(bad, want)
+
+
+# ----------------------------------------- the bitmap pass's row-loop digit
+
+def _clear(S, n, digs):
+    """Cells whose '*' neighbour in one of the digits (cell digit indices) is
+    set in S."""
+    A = S.reshape((3,) * n)
+    out = np.zeros_like(A)
+    for j in digs:
+        ax = n - 1 - j
+        star = np.take(A, [2], axis=ax)
+        for v in (0, 1):
+            idx = [slice(None)] * n
+            idx[ax] = slice(v, v + 1)
+            out[tuple(idx)] |= star
+    return out.reshape(-1)
+
+
+def _implicants(n, sup):
+    """Merge of every digit from the support: M(s) = every covered minterm in ON or DC."""
+    S = np.zeros(3 ** n, dtype=bool)
+    t = np.arange(1 << n)
+    rho = np.zeros_like(t)
+    for i in range(n):
+        rho += ((t >> i) & 1) * 3 ** i
+    S[rho] = sup
+    A = S.reshape((3,) * n)
+    for j in range(n):
+        ax = n - 1 - j
+        s0 = np.take(A, [0], axis=ax)
+        s1 = np.take(A, [1], axis=ax)
+        idx = [slice(None)] * n
+        idx[ax] = slice(2, 3)
+        A[tuple(idx)] = s0 & s1
+    return A.reshape(-1)
+
+
+@pytest.mark.parametrize("n,tile,nbr,seed,p_on,p_dc", [
+    (12, 7, 0, 1, 0.8, 0.0), (12, 7, 0, 2, 0.6, 0.1), (12, 4, 2, 3, 0.75, 0.05),
+    (11, 3, 2, 4, 0.85, 0.0), (10, 3, 1, 5, 0.5, 0.2), (12, 5, 2, 6, 0.9, 0.0)])
+def test_bitmap_pass_row_loop_digit_is_exact(n, tile, nbr, seed, p_on, p_dc):
+    """The bitmap pass reduces its tile digits but the top one in steps (each
+    step reading what the previous left), then, per row, clears a cell by its
+    neighbour group (read from the state the previous pass left, which had
+    the groups above reduced), its chunk digits (read from its row as the
+    steps left it) and its top tile digit, whose '*' row another thread may
+    be writing back at the same time: each bit of it is seen either as the
+    steps left it or final.  The result is the prime set for any such mix,
+    all-old and all-new included (Algorithm 3's ReduceAll, Section 4.1)."""
+    on, dc = synth.random_function(n, seed, p_on, p_dc)
+    sup = support(n, on, dc)
+    want = oracle.sweep(n, on, dc) != 0
+    H = n - C
+    tile_d = [C + j for j in range(tile)]              # high digits 0 .. tile-1
+    top = tile_d[-1]
+    nbr_d = [C + j for j in range(tile, tile + nbr)]   # the neighbour group
+    rest = [C + j for j in range(tile + nbr, H)]       # reduced by earlier passes
+    M = _implicants(n, sup)
+    S1 = M & ~_clear(M, n, rest)                       # the state the bitmap pass reads
+    T1 = S1.copy()
+    steps = [tile_d[:-1][i:i + 3] for i in range(0, len(tile_d) - 1, 3)]
+    for st in steps:
+        T1 = T1 & ~_clear(T1, n, st)
+    rng = np.random.default_rng(seed)
+    for mix in ("old", "new", "random", "random"):
+        if mix == "old":
+            X = T1
+        elif mix == "new":
+            X = want
+        else:
+            X = np.where(rng.random(T1.size) < 0.5, T1, want)
+        got = T1 & ~_clear(S1, n, nbr_d) & ~_clear(T1, n, list(range(C))) & ~_clear(X, n, [top])
+        assert np.array_equal(got, want), mix
+
+
+def test_row_loop_digit_model_catches_a_second_racy_digit():
+    """Planted mistake: read two tile digits from a mix of old and final
+    states (instead of one); some function then keeps a non-prime cell, so
+    the model above tells the one-digit argument from a wrong one."""
+    found = False
+    for seed in range(1, 40):
+        n = 9
+        on, dc = synth.random_function(n, seed, 0.8, 0.0)
+        sup = support(n, on, dc)
+        want = oracle.sweep(n, on, dc) != 0
+        tile_d = [C + j for j in range(4)]
+        M = _implicants(n, sup)
+        T1 = M & ~_clear(M, n, tile_d[:2])
+        X = want   # both racy digits read entirely final
+        got = T1 & ~_clear(T1, n, list(range(C))) & ~_clear(X, n, tile_d[2:])
+        if not np.array_equal(got, want):
+            found = True
+            break
+    assert found
